@@ -1,0 +1,431 @@
+/*
+ * osbf_oracle.c -- CPU oracle for the One-Sided Box Filter (arxiv 2108.05021).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct reference
+ * that the CUDA library is checked against.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it; the library
+ * itself never links, imports or calls it, and it shares no code, header or
+ * table with the CUDA path.
+ *
+ * What it computes (paper sections cited per function):
+ *   - the eight one-sided windows N1..N8 of Eq. (6)-(13), in frame coordinates
+ *     with x = column and y = row (rows increase downward);
+ *   - the box kernels k1..k8 of Sec. "One-sided Kernels for Box Filter": a plain
+ *     mean over the window, normalised by the full window size n_i (quadrants
+ *     (r+1)^2, half windows (r+1)(2r+1)); terms outside the padded frame are zero;
+ *   - Algorithm 2: d_i = mean_i - U, m = argmin_i |d_i| (first index in the tie
+ *     order wins), U <- U + d_m, all pixels from U^t (Jacobi), for `iters` passes;
+ *   - the appendix's boundary: replicate-pad the image by r once, iterate on the
+ *     padded frame (its ring evolves too), crop at the end.
+ * Arithmetic is FP64 (int64 for the exact 8-bit rule).  Window sums are direct
+ * summations over the window, no running sums, no integral images.
+ *
+ * Readings of the paper taken here (the paper is silent or self-inconsistent):
+ *   - `iters` passes (the appendix's `for it = 1:ItNum`), not IterationNum+1;
+ *   - tie order "paper": N1..N8; tie order "appendix": the appendix's difference
+ *     planes, i.e. N6, N5, N7, N8, N2, N1, N3, N4;
+ *   - the updated value is the selected mean itself (U + d_m in exact arithmetic).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL 1
+#define ORACLE_ENOMEM 2
+
+/* Storage rounding applied after every iteration (emulates a storage type). */
+#define ORACLE_STORE_NONE 0
+#define ORACLE_STORE_F32 1
+#define ORACLE_STORE_F16 2
+#define ORACLE_STORE_BF16 3
+
+/* Window offsets of Eq. (6)-(13).  Index 1..8.  dy = row offset, dx = column offset. */
+static void window_offsets(int i, int r, int *dy0, int *dy1, int *dx0, int *dx1) {
+    switch (i) {
+    case 1: *dx0 = -r; *dx1 = 0; *dy0 = 0;  *dy1 = r; break; /* x-r<=u<=x, y<=v<=y+r   */
+    case 2: *dx0 = 0;  *dx1 = r; *dy0 = 0;  *dy1 = r; break; /* x<=u<=x+r, y<=v<=y+r   */
+    case 3: *dx0 = 0;  *dx1 = r; *dy0 = -r; *dy1 = 0; break; /* x<=u<=x+r, y-r<=v<=y   */
+    case 4: *dx0 = -r; *dx1 = 0; *dy0 = -r; *dy1 = 0; break; /* x-r<=u<=x, y-r<=v<=y   */
+    case 5: *dx0 = -r; *dx1 = 0; *dy0 = -r; *dy1 = r; break; /* x-r<=u<=x, |y-v|<=r    */
+    case 6: *dx0 = 0;  *dx1 = r; *dy0 = -r; *dy1 = r; break; /* x<=u<=x+r, |y-v|<=r    */
+    case 7: *dx0 = -r; *dx1 = r; *dy0 = 0;  *dy1 = r; break; /* |u-x|<=r, y<=v<=y+r    */
+    default: *dx0 = -r; *dx1 = r; *dy0 = -r; *dy1 = 0; break; /* 8: |u-x|<=r, y-r<=v<=y */
+    }
+}
+
+static const int TIE_ORDER[2][8] = {
+    {1, 2, 3, 4, 5, 6, 7, 8}, /* paper numbering */
+    {6, 5, 7, 8, 2, 1, 3, 4}, /* appendix difference planes 1..8 */
+};
+
+/* Window size n_i = number of kernel taps of k_i (fixed, also at the frame edge). */
+static long window_count(int i, int r) {
+    int dy0, dy1, dx0, dx1;
+    window_offsets(i, r, &dy0, &dy1, &dx0, &dx1);
+    return (long)(dy1 - dy0 + 1) * (long)(dx1 - dx0 + 1);
+}
+
+/* Sum of V over window i around (y, x); pixels outside the FH x FW frame are zero. */
+static double window_sum_f64(const double *V, int FH, int FW, int y, int x, int i, int r) {
+    int dy0, dy1, dx0, dx1;
+    window_offsets(i, r, &dy0, &dy1, &dx0, &dx1);
+    int ya = y + dy0, yb = y + dy1, xa = x + dx0, xb = x + dx1;
+    if (ya < 0) ya = 0;
+    if (yb > FH - 1) yb = FH - 1;
+    if (xa < 0) xa = 0;
+    if (xb > FW - 1) xb = FW - 1;
+    double s = 0.0;
+    for (int yy = ya; yy <= yb; ++yy)
+        for (int xx = xa; xx <= xb; ++xx) s += V[(size_t)yy * FW + xx];
+    return s;
+}
+
+static int64_t window_sum_i64(const int64_t *V, int FH, int FW, int y, int x, int i, int r) {
+    int dy0, dy1, dx0, dx1;
+    window_offsets(i, r, &dy0, &dy1, &dx0, &dx1);
+    int ya = y + dy0, yb = y + dy1, xa = x + dx0, xb = x + dx1;
+    if (ya < 0) ya = 0;
+    if (yb > FH - 1) yb = FH - 1;
+    if (xa < 0) xa = 0;
+    if (xb > FW - 1) xb = FW - 1;
+    int64_t s = 0;
+    for (int yy = ya; yy <= yb; ++yy)
+        for (int xx = xa; xx <= xb; ++xx) s += V[(size_t)yy * FW + xx];
+    return s;
+}
+
+/* Round to the nearest value with `mant` fraction bits and minimum normal exponent
+ * `emin` (ties to even), i.e. IEEE binary16 (10, -14) or bfloat16 (7, -126).
+ * Written from the definition of round-to-nearest-even; no overflow handling is
+ * needed for the value ranges used here ([0, 255]). */
+static double round_binary(double v, int mant, int emin) {
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    (void)frexp(fabs(v), &e);       /* |v| = f * 2^e, f in [0.5, 1) */
+    int lead = e - 1;               /* exponent of the leading bit */
+    if (lead < emin) lead = emin;   /* subnormal range: fixed quantum */
+    double quantum = ldexp(1.0, lead - mant);
+    double q = rint(v / quantum);   /* default rounding mode: nearest, ties to even */
+    return q * quantum;
+}
+
+double oracle_round_storage(double v, int storage) {
+    switch (storage) {
+    case ORACLE_STORE_F32: return (double)(float)v;
+    case ORACLE_STORE_F16: return round_binary(v, 10, -14);
+    case ORACLE_STORE_BF16: return round_binary(v, 7, -126);
+    default: return v;
+    }
+}
+
+void oracle_round_storage_array(double *v, long n, int storage) {
+    for (long k = 0; k < n; ++k) v[k] = oracle_round_storage(v[k], storage);
+}
+
+int oracle_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* Replicate padding of one H x W plane into an (H+2r) x (W+2r) frame
+ * (the appendix's padarray(..., [r r], 'replicate')). */
+void oracle_pad_replicate_f64(const double *in, double *frame, int P, int H, int W, int r) {
+    int FH = H + 2 * r, FW = W + 2 * r;
+    for (int p = 0; p < P; ++p)
+        for (int fy = 0; fy < FH; ++fy) {
+            int y = fy - r;
+            if (y < 0) y = 0;
+            if (y > H - 1) y = H - 1;
+            for (int fx = 0; fx < FW; ++fx) {
+                int x = fx - r;
+                if (x < 0) x = 0;
+                if (x > W - 1) x = W - 1;
+                frame[((size_t)p * FH + fy) * FW + fx] = in[((size_t)p * H + y) * W + x];
+            }
+        }
+}
+
+/* The crop of the appendix's last line: frame rows/cols r .. r+H-1 / r .. r+W-1. */
+void oracle_crop_f64(const double *frame, double *out, int P, int H, int W, int r) {
+    int FH = H + 2 * r, FW = W + 2 * r;
+    for (int p = 0; p < P; ++p)
+        for (int y = 0; y < H; ++y)
+            memcpy(&out[((size_t)p * H + y) * W], &frame[((size_t)p * FH + y + r) * FW + r],
+                   sizeof(double) * (size_t)W);
+}
+
+/* The eight window means at every frame pixel (Eq. (6)-(13) with the box kernels
+ * k1..k8): means[(i-1)][p][y][x] = S_i / n_i, zero outside the frame. */
+void oracle_window_means_f64(const double *frame, double *means, int P, int FH, int FW, int r) {
+    size_t plane = (size_t)FH * FW;
+#pragma omp parallel for schedule(static)
+    for (long row = 0; row < (long)P * FH; ++row) {
+        int p = (int)(row / FH), y = (int)(row % FH);
+        const double *V = frame + (size_t)p * plane;
+        for (int x = 0; x < FW; ++x)
+            for (int i = 1; i <= 8; ++i)
+                means[(size_t)(i - 1) * P * plane + (size_t)p * plane + (size_t)y * FW + x] =
+                    window_sum_f64(V, FH, FW, y, x, i, r) / (double)window_count(i, r);
+    }
+}
+
+/*
+ * `iters` passes of Algorithm 2 on padded frames, in place.
+ *   frame   P x FH x FW, FP64, updated in place.
+ *   tie     0 = paper order N1..N8, 1 = appendix order.
+ *   maps    optional, iters x P x FH x FW: the selected window index (1..8).
+ *   gaps    optional, iters x P x FH x FW: the second-best |d| minus the best |d|,
+ *           taken over windows whose mean differs from the selected one (a pixel
+ *           whose windows all share one mean gets +inf).
+ *   hint    optional, iters x P x FH x FW window indices: the hinted window is taken
+ *           instead of this oracle's choice wherever its |d| is within `hint_thresh`
+ *           of the best |d| (a near tie); *n_hinted counts the pixels where that
+ *           changed the value.
+ *   storage rounding applied after every pass (ORACLE_STORE_*).
+ */
+int oracle_iterate_frame_f64(double *frame, int P, int FH, int FW, int r, int iters, int tie,
+                             uint8_t *maps, double *gaps, const uint8_t *hint, double hint_thresh,
+                             long long *n_hinted, int storage) {
+    if (P <= 0 || FH <= 0 || FW <= 0 || r < 0 || iters < 0 || tie < 0 || tie > 1) return ORACLE_EINVAL;
+    size_t plane = (size_t)FH * FW, total = (size_t)P * plane;
+    double *next = (double *)malloc(sizeof(double) * (total ? total : 1));
+    if (!next) return ORACLE_ENOMEM;
+    const int *order = TIE_ORDER[tie];
+    long long hinted = 0;
+    for (int t = 0; t < iters; ++t) {
+#pragma omp parallel for schedule(static) reduction(+ : hinted)
+        for (long row = 0; row < (long)P * FH; ++row) {
+            int p = (int)(row / FH), y = (int)(row % FH);
+            const double *V = frame + (size_t)p * plane;
+            for (int x = 0; x < FW; ++x) {
+                size_t idx = (size_t)p * plane + (size_t)y * FW + x;
+                double u = V[(size_t)y * FW + x];
+                double mean[9], ad[9];
+                for (int i = 1; i <= 8; ++i) {
+                    mean[i] = window_sum_f64(V, FH, FW, y, x, i, r) / (double)window_count(i, r);
+                    ad[i] = fabs(mean[i] - u);
+                }
+                int m = order[0];
+                for (int k = 1; k < 8; ++k)
+                    if (ad[order[k]] < ad[m]) m = order[k];
+                double gap = INFINITY;
+                for (int i = 1; i <= 8; ++i)
+                    if (i != m && mean[i] != mean[m] && ad[i] - ad[m] < gap) gap = ad[i] - ad[m];
+                size_t tidx = (size_t)t * total + idx;
+                if (hint) {
+                    int h = hint[tidx];
+                    if (h >= 1 && h <= 8 && h != m && ad[h] - ad[m] < hint_thresh) {
+                        if (mean[h] != mean[m]) hinted += 1;
+                        m = h;
+                    }
+                }
+                next[idx] = oracle_round_storage(mean[m], storage);
+                if (maps) maps[tidx] = (uint8_t)m;
+                if (gaps) gaps[tidx] = gap;
+            }
+        }
+        memcpy(frame, next, sizeof(double) * total);
+    }
+    free(next);
+    if (n_hinted) *n_hinted = hinted;
+    return ORACLE_OK;
+}
+
+/* The whole filter on P planes of H x W: pad, iterate, crop (the appendix). */
+int oracle_filter_f64(const double *in, double *out, int P, int H, int W, int r, int iters, int tie,
+                      uint8_t *maps, double *gaps, const uint8_t *hint, double hint_thresh,
+                      long long *n_hinted, int storage) {
+    if (P <= 0 || H <= 0 || W <= 0 || r < 0 || iters < 0) return ORACLE_EINVAL;
+    int FH = H + 2 * r, FW = W + 2 * r;
+    double *frame = (double *)malloc(sizeof(double) * (size_t)P * FH * FW);
+    if (!frame) return ORACLE_ENOMEM;
+    oracle_pad_replicate_f64(in, frame, P, H, W, r);
+    int st = oracle_iterate_frame_f64(frame, P, FH, FW, r, iters, tie, maps, gaps, hint, hint_thresh,
+                                      n_hinted, storage);
+    if (st == ORACLE_OK) oracle_crop_f64(frame, out, P, H, W, r);
+    free(frame);
+    return st;
+}
+
+/*
+ * Exact output of one plane on the output rectangle [y0, y1) x [x0, x1), computed
+ * from the dependency cone only: each pass widens the region a pixel depends on
+ * by r, so after `iters` passes the output there depends only on the frame pixels
+ * within iters*r of the rectangle.  Those are padded from `in` and iterated with
+ * zeros outside; pixels that the cut edges could affect lie outside the rectangle.
+ */
+int oracle_filter_region_f64(const double *in, int H, int W, int r, int iters, int tie, int y0, int y1,
+                             int x0, int x1, double *out) {
+    if (H <= 0 || W <= 0 || r < 0 || iters < 0 || y0 < 0 || x0 < 0 || y1 > H || x1 > W || y0 >= y1 ||
+        x0 >= x1)
+        return ORACLE_EINVAL;
+    int FH = H + 2 * r, FW = W + 2 * r;
+    long m = (long)iters * r;
+    long fy0 = y0 + r - m, fy1 = y1 + r + m, fx0 = x0 + r - m, fx1 = x1 + r + m;
+    if (fy0 < 0) fy0 = 0;
+    if (fx0 < 0) fx0 = 0;
+    if (fy1 > FH) fy1 = FH;
+    if (fx1 > FW) fx1 = FW;
+    int SH = (int)(fy1 - fy0), SW = (int)(fx1 - fx0);
+    double *sub = (double *)malloc(sizeof(double) * (size_t)SH * SW);
+    if (!sub) return ORACLE_ENOMEM;
+    for (int sy = 0; sy < SH; ++sy) {
+        int y = (int)fy0 + sy - r;
+        if (y < 0) y = 0;
+        if (y > H - 1) y = H - 1;
+        for (int sx = 0; sx < SW; ++sx) {
+            int x = (int)fx0 + sx - r;
+            if (x < 0) x = 0;
+            if (x > W - 1) x = W - 1;
+            sub[(size_t)sy * SW + sx] = in[(size_t)y * W + x];
+        }
+    }
+    int st = oracle_iterate_frame_f64(sub, 1, SH, SW, r, iters, tie, NULL, NULL, NULL, 0.0, NULL,
+                                      ORACLE_STORE_NONE);
+    if (st == ORACLE_OK)
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0; x < x1; ++x)
+                out[(size_t)(y - y0) * (x1 - x0) + (x - x0)] =
+                    sub[(size_t)(y + r - fy0) * SW + (x + r - fx0)];
+    free(sub);
+    return st;
+}
+
+/*
+ * The exact 8-bit rule for the first pass (the appendix casts to single, so the
+ * result is FP32): integer window sums S_i, and |mean_i - U| compared exactly by
+ * cross-multiplication, |S_i - n_i U| * n_j  vs  |S_j - n_j U| * n_i, in int64.
+ * The output is the correctly rounded FP32 value of S_m / n_m (both operands are
+ * exact in FP32 for r <= 32, so one IEEE division gives it).
+ *   in     P x H x W uint8;  frame_out  P x FH x FW float (the frame after pass 1);
+ *   map    optional P x FH x FW selected window index.
+ */
+int oracle_u8_first_pass(const uint8_t *in, float *frame_out, uint8_t *map, int P, int H, int W, int r,
+                         int tie) {
+    if (P <= 0 || H <= 0 || W <= 0 || r < 0 || r > 32 || tie < 0 || tie > 1) return ORACLE_EINVAL;
+    int FH = H + 2 * r, FW = W + 2 * r;
+    size_t plane = (size_t)FH * FW;
+    int64_t *V = (int64_t *)malloc(sizeof(int64_t) * (size_t)P * plane);
+    if (!V) return ORACLE_ENOMEM;
+    for (int p = 0; p < P; ++p)
+        for (int fy = 0; fy < FH; ++fy) {
+            int y = fy - r;
+            if (y < 0) y = 0;
+            if (y > H - 1) y = H - 1;
+            for (int fx = 0; fx < FW; ++fx) {
+                int x = fx - r;
+                if (x < 0) x = 0;
+                if (x > W - 1) x = W - 1;
+                V[(size_t)p * plane + (size_t)fy * FW + fx] = in[((size_t)p * H + y) * W + x];
+            }
+        }
+    const int *order = TIE_ORDER[tie];
+#pragma omp parallel for schedule(static)
+    for (long row = 0; row < (long)P * FH; ++row) {
+        int p = (int)(row / FH), y = (int)(row % FH);
+        const int64_t *Vp = V + (size_t)p * plane;
+        for (int x = 0; x < FW; ++x) {
+            int64_t u = Vp[(size_t)y * FW + x];
+            int64_t S[9], n[9], dev[9];
+            for (int i = 1; i <= 8; ++i) {
+                S[i] = window_sum_i64(Vp, FH, FW, y, x, i, r);
+                n[i] = window_count(i, r);
+                dev[i] = S[i] - n[i] * u;
+                if (dev[i] < 0) dev[i] = -dev[i];
+            }
+            int m = order[0];
+            for (int k = 1; k < 8; ++k) {
+                int i = order[k];
+                if (dev[i] * n[m] < dev[m] * n[i]) m = i; /* |d_i| < |d_m| exactly */
+            }
+            size_t idx = (size_t)p * plane + (size_t)y * FW + x;
+            frame_out[idx] = (float)S[m] / (float)n[m];
+            if (map) map[idx] = (uint8_t)m;
+        }
+    }
+    free(V);
+    return ORACLE_OK;
+}
+
+/*
+ * Transpose (adjoint) of the filter with every selection frozen to `maps`.
+ * With m(p) fixed, one pass is linear: U'(p) = (1/n_m(p)) * sum_{q in N_m(p), q in frame} U(q),
+ * so its transpose scatters g(p) / n_m(p) to every in-frame q of N_m(p).  The crop's
+ * transpose embeds grad_out into a zero frame; the replicate pad's transpose adds each
+ * frame pixel's gradient onto the image pixel it was copied from.
+ *   grad_out P x H x W, maps iters x P x FH x FW, grad_in P x H x W (written).
+ */
+int oracle_adjoint_f64(const double *grad_out, const uint8_t *maps, double *grad_in, int P, int H, int W,
+                       int r, int iters) {
+    if (P <= 0 || H <= 0 || W <= 0 || r < 0 || iters < 0) return ORACLE_EINVAL;
+    int FH = H + 2 * r, FW = W + 2 * r;
+    size_t plane = (size_t)FH * FW, total = (size_t)P * plane;
+    double *g = (double *)calloc(total ? total : 1, sizeof(double));
+    double *gn = (double *)calloc(total ? total : 1, sizeof(double));
+    if (!g || !gn) {
+        free(g);
+        free(gn);
+        return ORACLE_ENOMEM;
+    }
+    for (int p = 0; p < P; ++p)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                g[(size_t)p * plane + (size_t)(y + r) * FW + (x + r)] = grad_out[((size_t)p * H + y) * W + x];
+    for (int t = iters - 1; t >= 0; --t) {
+        memset(gn, 0, sizeof(double) * total);
+        /* scatter by planes so that planes can run in parallel without races */
+#pragma omp parallel for schedule(static)
+        for (int p = 0; p < P; ++p) {
+            for (int y = 0; y < FH; ++y)
+                for (int x = 0; x < FW; ++x) {
+                    size_t idx = (size_t)p * plane + (size_t)y * FW + x;
+                    int m = maps[(size_t)t * total + idx];
+                    int dy0, dy1, dx0, dx1;
+                    window_offsets(m, r, &dy0, &dy1, &dx0, &dx1);
+                    double w = g[idx] / (double)window_count(m, r);
+                    for (int yy = y + dy0; yy <= y + dy1; ++yy) {
+                        if (yy < 0 || yy >= FH) continue;
+                        for (int xx = x + dx0; xx <= x + dx1; ++xx) {
+                            if (xx < 0 || xx >= FW) continue;
+                            gn[(size_t)p * plane + (size_t)yy * FW + xx] += w;
+                        }
+                    }
+                }
+        }
+        double *tmp = g;
+        g = gn;
+        gn = tmp;
+    }
+    memset(grad_in, 0, sizeof(double) * (size_t)P * H * W);
+    for (int p = 0; p < P; ++p)
+        for (int fy = 0; fy < FH; ++fy) {
+            int y = fy - r;
+            if (y < 0) y = 0;
+            if (y > H - 1) y = H - 1;
+            for (int fx = 0; fx < FW; ++fx) {
+                int x = fx - r;
+                if (x < 0) x = 0;
+                if (x > W - 1) x = W - 1;
+                grad_in[((size_t)p * H + y) * W + x] += g[(size_t)p * plane + (size_t)fy * FW + fx];
+            }
+        }
+    free(g);
+    free(gn);
+    return ORACLE_OK;
+}

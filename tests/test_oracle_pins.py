@@ -1,0 +1,392 @@
+"""Pins of the CPU oracle against what the paper and plain mathematics fix.
+
+None of these tests compares the oracle with itself.  They check it against
+  * a hand-derived worked example (tests/golden/spike_r1.txt);
+  * a pure-Python brute force written from the set definitions of Eq. (6)-(13)
+    and Algorithm 2 (tiny frames only);
+  * the appendix's construction of the eight difference planes from 1D kernels
+    (k, k_L, k_R) evaluated with scipy's 2D convolution ('same' mode), with the
+    appendix's plane order as tie order;
+  * the classical box filter (scipy.ndimage.uniform_filter): half-window and
+    quadrant sums must recombine into it (the separable construction of the
+    section "Separable Kernels");
+  * fixed points the paper states: a flat region and noise-free ideal edges,
+    corners and checkerboards are preserved;
+  * exact rational arithmetic (fractions) for the 8-bit rule;
+  * the transpose identity <A v, w> = <v, A^T w> and central finite differences
+    for the adjoint;
+  * torch's own f16 / bf16 conversions for the storage rounding.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+import scipy.signal as sps
+
+import oracle
+from paper_2108_05021_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------------
+# independent brute force: Eq. (6)-(13) as set predicates, Algorithm 2, appendix frame
+# ----------------------------------------------------------------------------------
+def _in_window(i, r, x, y, u, v):
+    """(u, v) in N_i(x, y), u = column, v = row -- typed from Eq. (6)-(13)."""
+    return {
+        1: x - r <= u <= x and y <= v <= y + r,
+        2: x <= u <= x + r and y <= v <= y + r,
+        3: x <= u <= x + r and y - r <= v <= y,
+        4: x - r <= u <= x and y - r <= v <= y,
+        5: x - r <= u <= x and abs(y - v) <= r,
+        6: x <= u <= x + r and abs(y - v) <= r,
+        7: abs(u - x) <= r and y <= v <= y + r,
+        8: abs(u - x) <= r and y - r <= v <= y,
+    }[i]
+
+
+def _kernel_weight(i, r):
+    # weights of k1..k4 are (r+1)^-2, of k5..k8 (r+1)^-1 (2r+1)^-1
+    return Fraction(1, (r + 1) ** 2) if i <= 4 else Fraction(1, (r + 1) * (2 * r + 1))
+
+
+def brute_force(img, r, iters, order=(1, 2, 3, 4, 5, 6, 7, 8)):
+    H, W = len(img), len(img[0])
+    FH, FW = H + 2 * r, W + 2 * r
+    U = [[img[min(max(fy - r, 0), H - 1)][min(max(fx - r, 0), W - 1)] for fx in range(FW)] for fy in range(FH)]
+    for _ in range(iters):
+        new = [[0.0] * FW for _ in range(FH)]
+        for y in range(FH):
+            for x in range(FW):
+                best, best_ad = None, None
+                for i in order:
+                    s = 0.0
+                    for v in range(y - r, y + r + 1):
+                        for u in range(x - r, x + r + 1):
+                            if 0 <= v < FH and 0 <= u < FW and _in_window(i, r, x, y, u, v):
+                                s += U[v][u]
+                    mean = s * float(_kernel_weight(i, r))
+                    ad = abs(mean - U[y][x])
+                    if best is None or ad < best_ad:
+                        best, best_ad = mean, ad
+                new[y][x] = best
+        U = new
+    return np.array([row[r:r + W] for row in U[r:r + H]])
+
+
+# ----------------------------------------------------------------------------------
+def test_golden_spike():
+    rows = np.loadtxt(os.path.join(GOLDEN, "spike_r1.txt"), comments="#")
+    for it, *expect in rows:
+        got = oracle.filter(np.array([[0.0, 1.0, 0.0]]), r=1, iters=int(it))["out"]
+        np.testing.assert_array_equal(got, np.array([expect]))
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 5), (4, 1), (3, 4), (5, 6)])
+def test_brute_force_matches(shape, r):
+    rng = np.random.default_rng(hash((shape, r)) % 2**32)
+    img = rng.random(shape)
+    iters = 2
+    want = brute_force(img.tolist(), r, iters)
+    got = oracle.filter(img, r, iters)["out"]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_brute_force_appendix_order():
+    rng = np.random.default_rng(7)
+    img = np.round(rng.random((4, 5)) * 4) / 4  # many exact ties
+    want = brute_force(img.tolist(), 1, 2, order=(6, 5, 7, 8, 2, 1, 3, 4))
+    got = oracle.filter(img, 1, 2, tie="appendix")["out"]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+    want_p = brute_force(img.tolist(), 1, 2)
+    got_p = oracle.filter(img, 1, 2, tie="paper")["out"]
+    np.testing.assert_allclose(got_p, want_p, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------
+# the appendix's construction: 1D kernels, 2D convolution 'same', min(|d|) first index
+# ----------------------------------------------------------------------------------
+def appendix_planes(im, r):
+    """d-planes of the appendix: conv2(col_kernel, row_kernel, im, 'same') - im."""
+    k = np.ones(2 * r + 1) / (2 * r + 1)
+    kl = k.copy()
+    kl[r + 1:] = 0.0
+    kl /= kl.sum()
+    kr = kl[::-1].copy()
+    pairs = [(k, kl), (k, kr), (kl, k), (kr, k), (kl, kl), (kl, kr), (kr, kl), (kr, kr)]
+    return np.stack([sps.convolve2d(im, np.outer(a, b), mode="same") - im for a, b in pairs])
+
+
+def appendix_filter(img, r, iters):
+    im = np.pad(img, r, mode="edge")
+    for _ in range(iters):
+        d = appendix_planes(im, r)
+        ind = np.argmin(np.abs(d), axis=0)  # first index wins on ties
+        im = im + np.take_along_axis(d, ind[None], axis=0)[0]
+    return im[r:-r or None, r:-r or None] if r else im
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 5])
+def test_appendix_convolution_semantics(r):
+    rng = np.random.default_rng(100 + r)
+    img = rng.random((17, 23))
+    for iters in (1, 3):
+        want = appendix_filter(img, r, iters)
+        got = oracle.filter(img, r, iters, tie="appendix")["out"]
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------
+# the classical box filter recovered from the one-sided sums
+# ----------------------------------------------------------------------------------
+def _shift_sum(f, axis, shifts):
+    """sum_k f shifted by +k along `axis` (out[i] = sum_k f[i - k]), zero outside."""
+    out = np.zeros_like(f)
+    n = f.shape[axis]
+    for k in shifts:
+        src = [slice(None)] * 2
+        dst = [slice(None)] * 2
+        if k >= 0:
+            src[axis], dst[axis] = slice(0, n - k), slice(k, n)
+        else:
+            src[axis], dst[axis] = slice(-k, n), slice(0, n + k)
+        out[tuple(dst)] += f[tuple(src)]
+    return out
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 4])
+def test_box_filter_recovered(r):
+    rng = np.random.default_rng(200 + r)
+    frame = rng.random((2, 13, 19))
+    m = oracle.window_means(frame, r)
+    nq, nh, nb = (r + 1) ** 2, (r + 1) * (2 * r + 1), (2 * r + 1) ** 2
+    S = np.stack([m[i] * (nq if i < 4 else nh) for i in range(8)])
+    for p in range(frame.shape[0]):
+        f = frame[p]
+        box = ndi.uniform_filter(f, size=2 * r + 1, mode="constant", cval=0.0) * nb
+        row = ndi.uniform_filter1d(f, size=2 * r + 1, axis=1, mode="constant", cval=0.0) * (2 * r + 1)
+        col = ndi.uniform_filter1d(f, size=2 * r + 1, axis=0, mode="constant", cval=0.0) * (2 * r + 1)
+        s = S[:, p]
+        np.testing.assert_allclose(s[4] + s[5] - col, box, atol=1e-10)  # left + right halves
+        np.testing.assert_allclose(s[6] + s[7] - row, box, atol=1e-10)  # down + up halves
+        np.testing.assert_allclose(s[0] + s[1] + s[2] + s[3] - row - col - f, box, atol=1e-10)
+        # a half window is the union of its two quadrants minus their shared segment
+        row_left = _shift_sum(f, axis=1, shifts=range(0, r + 1))     # f(y, x-k), k = 0..r
+        col_down = _shift_sum(f, axis=0, shifts=range(-r, 1))        # f(y+k, x), k = 0..r
+        np.testing.assert_allclose(s[0] + s[3] - row_left, s[4], atol=1e-10)  # N1 u N4 = N5
+        np.testing.assert_allclose(s[0] + s[1] - col_down, s[6], atol=1e-10)  # N1 u N2 = N7
+
+
+@pytest.mark.parametrize("r", [1, 3])
+def test_window_geometry_symmetries(r):
+    """Mirroring the frame permutes the eight windows as their definitions imply."""
+    rng = np.random.default_rng(300 + r)
+    f = rng.random((11, 14))
+    m = oracle.window_means(f, r)[:, 0]
+    mx = oracle.window_means(f[:, ::-1].copy(), r)[:, 0][:, :, ::-1]  # flip x
+    my = oracle.window_means(f[::-1, :].copy(), r)[:, 0][:, ::-1, :]  # flip y
+    mt = oracle.window_means(f.T.copy(), r)[:, 0].transpose(0, 2, 1)  # swap x and y
+    flip_x = {1: 2, 2: 1, 3: 4, 4: 3, 5: 6, 6: 5, 7: 7, 8: 8}
+    flip_y = {1: 4, 4: 1, 2: 3, 3: 2, 5: 5, 6: 6, 7: 8, 8: 7}
+    swap = {1: 3, 3: 1, 2: 2, 4: 4, 5: 8, 8: 5, 6: 7, 7: 6}
+    for i in range(1, 9):
+        np.testing.assert_allclose(mx[flip_x[i] - 1], m[i - 1], atol=1e-12)
+        np.testing.assert_allclose(my[flip_y[i] - 1], m[i - 1], atol=1e-12)
+        np.testing.assert_allclose(mt[swap[i] - 1], m[i - 1], atol=1e-12)
+
+
+def test_window_means_constant_interior():
+    r = 2
+    f = np.ones((9, 9))
+    m = oracle.window_means(f, r)[:, 0]
+    np.testing.assert_array_equal(m[:, r:-r, r:-r], np.ones((8, 5, 5)))
+
+
+# ----------------------------------------------------------------------------------
+# fixed points: flat regions, ideal edges, corners, checkerboards (edge preservation)
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("r", [0, 1, 2, 5])
+@pytest.mark.parametrize("tie", ["paper", "appendix"])
+def test_constant_is_fixed_point(r, tie):
+    img = np.full((2, 7, 10), 0.5)
+    out = oracle.filter(img, r, 4, tie=tie)["out"]
+    np.testing.assert_array_equal(out, img)
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_step_edges_and_corner_preserved(r):
+    H, W = 24, 30
+    v = np.full((H, W), 0.25)
+    v[:, 13:] = 0.75  # vertical step at column 13 >= r
+    h = np.full((H, W), 0.25)
+    h[11:, :] = 0.75
+    corner = np.full((H, W), 0.25)
+    corner[10:, 12:] = 0.75  # L-shaped corner
+    rect = np.full((H, W), 0.25)
+    rect[5:5 + 2 * r + 3, 7:7 + 2 * r + 1] = 0.75  # rectangle of sides >= 2r
+    for img in (v, h, corner, rect):
+        out = oracle.filter(img, r, 6)["out"]
+        np.testing.assert_array_equal(out, img)
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (2, 4), (3, 7)])
+def test_checkerboard_preserved(r, s):
+    img = synth.checkerboard(4 * s, 5 * s, s).astype(np.float64)
+    out = oracle.filter(img, r, 5)["out"]
+    np.testing.assert_array_equal(out, img)
+
+
+def test_box_filter_smooths_edges_but_osbf_does_not():
+    """Contrast with the classical box filter (Fig. 1): a box filter blurs a step."""
+    img = np.full((16, 16), 0.25)
+    img[:, 8:] = 0.75
+    box = ndi.uniform_filter(np.pad(img, 2, mode="edge"), size=5, mode="constant")[2:-2, 2:-2]
+    assert np.abs(box - img).max() > 0.1
+    np.testing.assert_array_equal(oracle.filter(img, 2, 3)["out"], img)
+
+
+def test_noise_is_smoothed():
+    """Sanity check (not a pin): one large rectangle plus noise gets closer to the clean scene."""
+    img = synth.piecewise_stack(1, 1, 64, 64, seed=3, sigma=0.05, n_rect=1, n_tri=0)[0, 0].astype(np.float64)
+    clean = synth.piecewise_stack(1, 1, 64, 64, seed=3, sigma=0.0, n_rect=1, n_tri=0)[0, 0].astype(np.float64)
+    out = oracle.filter(img, 2, 10)["out"]
+    assert np.sqrt(np.mean((out - clean) ** 2)) < 0.5 * np.sqrt(np.mean((img - clean) ** 2))
+
+
+# ----------------------------------------------------------------------------------
+# exact 8-bit rule
+# ----------------------------------------------------------------------------------
+def fraction_first_pass(img, r, order=(1, 2, 3, 4, 5, 6, 7, 8)):
+    H, W = img.shape
+    FH, FW = H + 2 * r, W + 2 * r
+    U = [[int(img[min(max(fy - r, 0), H - 1)][min(max(fx - r, 0), W - 1)]) for fx in range(FW)] for fy in range(FH)]
+    out = np.zeros((FH, FW), dtype=np.float32)
+    mp = np.zeros((FH, FW), dtype=np.uint8)
+    for y in range(FH):
+        for x in range(FW):
+            best, best_ad, best_i = None, None, None
+            for i in order:
+                s = sum(U[v][u] for v in range(max(0, y - r), min(FH, y + r + 1))
+                        for u in range(max(0, x - r), min(FW, x + r + 1)) if _in_window(i, r, x, y, u, v))
+                mean = Fraction(s) * _kernel_weight(i, r)
+                ad = abs(mean - U[y][x])
+                if best is None or ad < best_ad:
+                    best, best_ad, best_i = mean, ad, i
+            out[y, x] = np.float32(float(best))  # double rounding is innocuous here (53 >= 2*24+2)
+            mp[y, x] = best_i
+    return out, mp
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_u8_exact_rule(r):
+    rng = np.random.default_rng(400 + r)
+    img = rng.integers(0, 256, size=(5, 7), dtype=np.uint8)
+    img[1:3, 2:5] = 17  # plateaus create exact ties
+    frame, mp = oracle.u8_first_pass(img, r)
+    want, want_map = fraction_first_pass(img, r)
+    np.testing.assert_array_equal(frame[0].view(np.uint32), want.view(np.uint32))
+    np.testing.assert_array_equal(mp[0], want_map)
+    frame_a, mp_a = oracle.u8_first_pass(img, r, tie="appendix")
+    want_a, want_map_a = fraction_first_pass(img, r, order=(6, 5, 7, 8, 2, 1, 3, 4))
+    np.testing.assert_array_equal(frame_a[0].view(np.uint32), want_a.view(np.uint32))
+    np.testing.assert_array_equal(mp_a[0], want_map_a)
+
+
+def test_u8_spike():
+    frame, _ = oracle.u8_first_pass(np.array([[0, 255, 0]], dtype=np.uint8), 1)
+    assert oracle.crop(frame, 1)[0].tolist() == [[0.0, 127.5, 0.0]]
+
+
+# ----------------------------------------------------------------------------------
+# adjoint: transpose identity and finite differences
+# ----------------------------------------------------------------------------------
+def _frozen_apply(v, maps, r, iters):
+    # hint_thresh = inf forces every selection to the given map: the frozen linear map A
+    return oracle.filter(v, r, iters, hint=maps, hint_thresh=np.inf)["out"]
+
+
+@pytest.mark.parametrize("r,iters", [(1, 1), (1, 3), (2, 2), (3, 2)])
+def test_adjoint_transpose_identity(r, iters):
+    rng = np.random.default_rng(500 + r * 10 + iters)
+    x = rng.random((2, 9, 11))
+    maps = oracle.filter(x, r, iters, want_maps=True)["maps"]
+    v = rng.standard_normal(x.shape)
+    w = rng.standard_normal(x.shape)
+    Av = _frozen_apply(v, maps, r, iters)
+    Atw = oracle.adjoint(w, maps, r, iters)
+    assert abs(np.sum(Av * w) - np.sum(v * Atw)) < 1e-10 * (1 + abs(np.sum(Av * w)))
+
+
+def test_frozen_map_is_the_filter_on_its_own_input():
+    rng = np.random.default_rng(9)
+    x = rng.random((1, 8, 8))
+    res = oracle.filter(x, 2, 3, want_maps=True)
+    np.testing.assert_allclose(_frozen_apply(x, res["maps"], 2, 3), res["out"], atol=1e-14)
+
+
+def test_adjoint_finite_differences():
+    """FP64 central differences on 1 x 1 x 32 x 32, r = 1, 2 passes, away from selection ties."""
+    rng = np.random.default_rng(11)
+    x = synth.piecewise_plane(32, 32, seed=5, sigma=0.05).astype(np.float64)
+    w = rng.standard_normal((32, 32))
+    r, iters, h = 1, 2, 1e-6
+    base = oracle.filter(x, r, iters, want_maps=True)
+    g = oracle.adjoint(w, base["maps"], r, iters)
+    checked = 0
+    for (y, xx) in itertools.product(range(0, 32, 3), range(0, 32, 3)):
+        xp, xm = x.copy(), x.copy()
+        xp[y, xx] += h
+        xm[y, xx] -= h
+        rp = oracle.filter(xp, r, iters, want_maps=True)
+        rm = oracle.filter(xm, r, iters, want_maps=True)
+        if not (np.array_equal(rp["maps"], base["maps"]) and np.array_equal(rm["maps"], base["maps"])):
+            continue  # the perturbation flips a selection: not differentiable there
+        fd = (np.sum(rp["out"] * w) - np.sum(rm["out"] * w)) / (2 * h)
+        assert abs(fd - g[y, xx]) < 1e-6 * (1 + abs(g[y, xx]))
+        checked += 1
+    assert checked > 50
+
+
+# ----------------------------------------------------------------------------------
+# region oracle, hints, storage rounding
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("r,iters", [(1, 3), (2, 2), (3, 1)])
+def test_region_matches_full(r, iters):
+    x = synth.piecewise_plane(40, 37, seed=r + iters, sigma=0.05).astype(np.float64)
+    full = oracle.filter(x, r, iters)["out"]
+    for (y0, y1, x0, x1) in [(0, 5, 0, 7), (10, 20, 11, 30), (35, 40, 30, 37), (0, 40, 0, 37), (17, 18, 0, 1)]:
+        np.testing.assert_array_equal(oracle.filter_region(x, r, iters, y0, y1, x0, x1), full[y0:y1, x0:x1])
+
+
+def test_hint_with_own_maps_changes_nothing():
+    x = synth.piecewise_plane(30, 30, seed=1).astype(np.float64)
+    res = oracle.filter(x, 2, 3, want_maps=True)
+    again = oracle.filter(x, 2, 3, hint=res["maps"], hint_thresh=1e-6)
+    np.testing.assert_array_equal(again["out"], res["out"])
+    assert again["n_hinted"] == 0
+
+
+def test_storage_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    v = np.concatenate([rng.random(20000), rng.random(2000) * 255, [0.0, 1.0, 0.5, 1 / 3, 2**-20, 2**-25]])
+    # exact halfway cases between neighbouring f16 / bf16 values
+    v = np.concatenate([v, (np.arange(1, 200) * 2 + 1) * 2.0**-11, (np.arange(1, 200) * 2 + 1) * 2.0**-8])
+    # float32-representable values, so that torch's float32 -> 16-bit conversion is one
+    # correctly rounded step (its float64 -> 16-bit path rounds through float32 first)
+    v = v.astype(np.float32).astype(np.float64)
+    for st, tdt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
+        want = torch.from_numpy(v.astype(np.float32)).to(tdt).to(torch.float64).numpy()
+        np.testing.assert_array_equal(oracle.round_storage(v, st), want)
+    np.testing.assert_array_equal(oracle.round_storage(v, "f32"), v.astype(np.float32).astype(np.float64))
+
+
+def test_storage_rounded_filter_stays_on_grid():
+    x = synth.round_to_storage(synth.piecewise_plane(20, 20, seed=2), "f16").astype(np.float64)
+    out = oracle.filter(x, 2, 3, storage="f16")["out"]
+    np.testing.assert_array_equal(oracle.round_storage(out, "f16"), out)
