@@ -1,0 +1,173 @@
+/*
+ * osbf.h -- C ABI of the GB300 One-Sided Box Filter library (libosbf.so).
+ *
+ * The filter is the One-Sided Box Filter of Gong, "One-Sided Box Filter for Edge
+ * Preserving Image Smoothing" (arxiv 2108.05021):
+ *   - Eq. (1): U = Phi(I(N(x, y))), here Phi = mean over one of eight windows;
+ *   - Eq. (6)-(13): the eight one-sided windows N1..N8 of radius r around (x, y)
+ *     (N1-N4 quadrants of (r+1)^2 pixels, N5-N8 half windows of (r+1)(2r+1));
+ *   - Sec. "One-sided Kernels for Box Filter": the box kernels k1..k8 (a window
+ *     mean normalised by the full window size);
+ *   - Algorithm 2: d_i = k_i (x) U - U, m = argmin_i |d_i|, U <- U + d_m, repeated;
+ *   - the appendix listing: the image is replicate-padded by r once, every pass
+ *     runs on the padded frame with zeros beyond it (the frame's ring evolves
+ *     too), and the result is the frame cropped back to H x W.
+ * Coordinates: x = column (the W axis), y = row (the H axis, increasing down).
+ * `iters` passes are run (the appendix's loop count).  Ties in |d_i| go to the
+ * first window in the tie order (OSBF_TIE_PAPER: N1..N8; OSBF_TIE_APPENDIX:
+ * the appendix's difference planes N6, N5, N7, N8, N2, N1, N3, N4).
+ *
+ * Conventions for every entry point:
+ *   - Images are N x C x H x W, contiguous, row-major (NCHW).  Every channel is a
+ *     separate plane, filtered independently (the appendix loops over channels).
+ *   - Unless a function says otherwise, image, gradient and map pointers are
+ *     DEVICE pointers on the context's device, owned by the caller, and must not
+ *     alias each other.
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = the legacy default
+ *     stream) and is asynchronous unless stated otherwise.
+ *   - Errors come back as osbf_status codes; no exception crosses the ABI.  The
+ *     text of the last error of a context is returned by osbf_last_error().
+ *   - A context is not thread-safe: use one context per host thread.
+ *   - Radii 0..OSBF_MAX_RADIUS are supported; larger r gives OSBF_EUNSUPPORTED.
+ *     r = 0 or iters = 0 returns the input unchanged (converted to the output
+ *     type for 8-bit input).
+ */
+#ifndef OSBF_H
+#define OSBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OSBF_MAX_RADIUS 16
+#define OSBF_MAX_DEPTH 8
+
+typedef enum {
+    OSBF_OK = 0,
+    OSBF_EINVAL = 1,       /* a bad argument (null pointer, non-positive size, aliasing, ...) */
+    OSBF_ENOMEM = 2,       /* a workspace allocation failed */
+    OSBF_ECUDA = 3,        /* a CUDA runtime or driver call failed */
+    OSBF_EUNSUPPORTED = 4, /* valid but not supported (r > OSBF_MAX_RADIUS, dtype, ...) */
+    OSBF_ETIMEOUT = 5      /* a bounded device-side wait gave up (batched launch) */
+} osbf_status;
+
+typedef enum {
+    OSBF_F32 = 0,  /* float32 storage and arithmetic */
+    OSBF_F16 = 1,  /* float16 storage; sums and scores in float32, rounded to f16 after every pass */
+    OSBF_BF16 = 2, /* bfloat16 storage; as OSBF_F16 */
+    OSBF_U8 = 3    /* uint8 input, float32 output; first pass exact in integers (see below) */
+} osbf_dtype;
+
+typedef enum { OSBF_TIE_PAPER = 0, OSBF_TIE_APPENDIX = 1 } osbf_tie;
+
+typedef struct osbf_ctx osbf_ctx;
+
+/* Per-call options of osbf_filter_ex().  Zero-initialise, then set fields. */
+typedef struct {
+    int depth;       /* passes fused per launch (temporal blocking), 1..OSBF_MAX_DEPTH;
+                        0 = the tuned choice for (dtype, r, size) */
+    int tie;         /* osbf_tie */
+    uint8_t *maps;   /* optional device buffer, iters x N*C x (H+2r) x (W+2r) bytes: the
+                        selected window index (1..8 = N1..N8) of every frame pixel and pass */
+    int reserved[4]; /* must be zero */
+} osbf_options;
+
+/* Create a context on CUDA device `device`.  *out receives it.  The context owns
+ * workspaces (two padded frames per shape class, grown on demand), the tuned
+ * choices and the batched launch's graphs; osbf_destroy() frees them. */
+osbf_status osbf_create(osbf_ctx **out, int device);
+
+/* Destroy a context (synchronises the device first).  NULL is ignored. */
+void osbf_destroy(osbf_ctx *ctx);
+
+/* Text of the last error recorded in `ctx` ("" if none).  Valid until the next call. */
+const char *osbf_last_error(const osbf_ctx *ctx);
+
+/*
+ * Forward filter (Algorithm 2 with the appendix's boundary; see the file comment).
+ *   in    N x C x H x W, element type per `dtype` (uint8 for OSBF_U8).
+ *   out   N x C x H x W, same element type as `in`, except float32 for OSBF_U8
+ *         (the appendix works in single precision).
+ * OSBF_U8: the first pass is exact: integer window sums S_i, the selection
+ * compares |S_i - n_i U| n_j with |S_j - n_j U| n_i in int64, and the new value is
+ * the correctly rounded float32 of S_m / n_m; later passes run in float32.
+ * Returns OSBF_EINVAL for null pointers, N, C, H or W <= 0, r or iters < 0, or
+ * in == out; OSBF_EUNSUPPORTED for r > OSBF_MAX_RADIUS.
+ */
+osbf_status osbf_filter(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
+                        osbf_dtype dtype, void *stream);
+
+/* osbf_filter() with options (fused depth, tie order, selection maps).  opts may be NULL. */
+osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
+                           osbf_dtype dtype, const osbf_options *opts, void *stream);
+
+/*
+ * osbf_filter() on HOST buffers: copies `in` to the device, filters, copies the
+ * result into `out`, and returns when `out` is filled (synchronous).  Pinned host
+ * memory gives the fastest copies.  The device buffers are owned by the context.
+ */
+osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
+                             osbf_dtype dtype, void *stream);
+
+/*
+ * Backward (vector-Jacobian product) of the float32 forward, with each pixel's
+ * selection frozen to the map stored by the forward (the selection is piecewise
+ * constant, so this is the exact gradient wherever no |d_i| tie is crossed).
+ * With the selection frozen one pass is linear, U'(p) = (1/n_m(p)) sum_{q in
+ * N_m(p) inside the frame} U(q), so its transpose scatters g(p)/n_m(p) over the
+ * window; the crop's transpose embeds the gradient into a zero frame and the
+ * replicate pad's transpose folds the ring back onto the edge pixels.
+ *   grad_out  N x C x H x W float32.      grad_in  N x C x H x W float32 (written).
+ *   maps      iters x N*C x (H+2r) x (W+2r) uint8, as written by osbf_filter_ex().
+ */
+osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps,
+                                 int N, int C, int H, int W, int r, int iters, void *stream);
+
+/*
+ * Backward from checkpoints: instead of every pass's map, the forward kept the
+ * padded frame before every `interval`-th pass (ceil(iters/interval) frames of
+ * N*C x (H+2r) x (W+2r) float32, frame k = state before pass k*interval, as written by
+ * osbf_filter_checkpointed()).  Each segment's maps are recomputed from its
+ * checkpoint into context workspace, then the segment is back-propagated.
+ */
+osbf_status osbf_filter_checkpointed(osbf_ctx *ctx, const float *in, float *out, float *checkpoints, int interval,
+                                     int N, int C, int H, int W, int r, int iters, void *stream);
+osbf_status osbf_filter_backward_checkpointed(osbf_ctx *ctx, const float *grad_out, float *grad_in,
+                                              const float *checkpoints, int interval, int N, int C, int H, int W,
+                                              int r, int iters, void *stream);
+
+/* One image of a batched call: a single H x W float32 plane, its radius and pass count. */
+typedef struct {
+    const float *in; /* device, H x W */
+    float *out;      /* device, H x W */
+    int H, W, r, iters;
+} osbf_job;
+
+/*
+ * Filter `njobs` independent images of different sizes, radii and pass counts in
+ * one persistent launch (a device-side queue of tiles; a job's next fused group
+ * starts once its previous group has finished), replayed from a CUDA graph that
+ * the context caches per job signature.  Equivalent to one osbf_filter() per job
+ * (float32, paper tie order).  Returns OSBF_ETIMEOUT if a bounded device-side
+ * wait gave up (the outputs are then undefined); the context stays usable.
+ */
+osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream);
+
+/* Tune the fused depth for (dtype, r) on an H x W x planes problem by timing the
+ * candidates on the device (synchronous); later calls with depth 0 use it. */
+osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int iters);
+
+/* Number of kernel launches the last filter call on `ctx` enqueued. */
+int osbf_last_launch_count(const osbf_ctx *ctx);
+
+/* Library version string. */
+const char *osbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSBF_H */

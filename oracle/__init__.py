@@ -62,7 +62,7 @@ def _load():
         lib.oracle_filter_f64.restype = i
         lib.oracle_filter_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, vp, d, vp, i]
         lib.oracle_filter_region_f64.restype = i
-        lib.oracle_filter_region_f64.argtypes = [vp, i, i, i, i, i, i, i, i, i, vp]
+        lib.oracle_filter_region_f64.argtypes = [vp, i, i, i, i, i, i, i, i, i, vp, vp, i, d, vp]
         lib.oracle_u8_first_pass.restype = i
         lib.oracle_u8_first_pass.argtypes = [vp, vp, vp, i, i, i, i, i]
         lib.oracle_adjoint_f64.restype = i
@@ -165,13 +165,23 @@ def filter(x: np.ndarray, r: int, iters: int, tie: str = "paper", want_maps: boo
 
 
 def filter_region(plane: np.ndarray, r: int, iters: int, y0: int, y1: int, x0: int, x1: int,
-                  tie: str = "paper") -> np.ndarray:
-    """Exact output of one H x W plane on [y0, y1) x [x0, x1), from the dependency cone only."""
+                  tie: str = "paper", hint: Optional[np.ndarray] = None, hint_thresh: float = 1e-6,
+                  return_hinted: bool = False):
+    """Exact output of one H x W plane on [y0, y1) x [x0, x1), from the dependency cone only.
+
+    `hint`: optional selection maps of this plane's whole frame, iters x (H+2r) x (W+2r)
+    (any array supporting the buffer protocol, e.g. a numpy memmap or array).
+    """
     p = np.ascontiguousarray(plane, dtype=np.float64)
     H, W = p.shape
     out = np.empty((y1 - y0, x1 - x0), dtype=np.float64)
-    _check(_load().oracle_filter_region_f64(_ptr(p), H, W, r, iters, TIE[tie], y0, y1, x0, x1, _ptr(out)))
-    return out
+    h = None
+    if hint is not None:
+        h = np.ascontiguousarray(hint, dtype=np.uint8).reshape(iters, H + 2 * r, W + 2 * r)
+    nh = ctypes.c_longlong(0)
+    _check(_load().oracle_filter_region_f64(_ptr(p), H, W, r, iters, TIE[tie], y0, y1, x0, x1, _ptr(out), _ptr(h),
+                                            W + 2 * r, float(hint_thresh), ctypes.addressof(nh)))
+    return (out, int(nh.value)) if return_hinted else out
 
 
 def u8_first_pass(x: np.ndarray, r: int, tie: str = "paper"):

@@ -269,9 +269,12 @@ int oracle_filter_f64(const double *in, double *out, int P, int H, int W, int r,
  * by r, so after `iters` passes the output there depends only on the frame pixels
  * within iters*r of the rectangle.  Those are padded from `in` and iterated with
  * zeros outside; pixels that the cut edges could affect lie outside the rectangle.
+ * `hint` (optional): the selection maps of the whole frame, iters x FH x hint_pitch,
+ * applied as in oracle_iterate_frame_f64.
  */
 int oracle_filter_region_f64(const double *in, int H, int W, int r, int iters, int tie, int y0, int y1,
-                             int x0, int x1, double *out) {
+                             int x0, int x1, double *out, const uint8_t *hint, int hint_pitch, double hint_thresh,
+                             long long *n_hinted) {
     if (H <= 0 || W <= 0 || r < 0 || iters < 0 || y0 < 0 || x0 < 0 || y1 > H || x1 > W || y0 >= y1 ||
         x0 >= x1)
         return ORACLE_EINVAL;
@@ -296,8 +299,22 @@ int oracle_filter_region_f64(const double *in, int H, int W, int r, int iters, i
             sub[(size_t)sy * SW + sx] = in[(size_t)y * W + x];
         }
     }
-    int st = oracle_iterate_frame_f64(sub, 1, SH, SW, r, iters, tie, NULL, NULL, NULL, 0.0, NULL,
+    /* optional hints: the full frame's maps (iters x FH x hint_pitch), cut to the sub-frame */
+    uint8_t *subhint = NULL;
+    if (hint) {
+        subhint = (uint8_t *)malloc((size_t)iters * SH * SW + 1);
+        if (!subhint) {
+            free(sub);
+            return ORACLE_ENOMEM;
+        }
+        for (int t = 0; t < iters; ++t)
+            for (int sy = 0; sy < SH; ++sy)
+                memcpy(&subhint[((size_t)t * SH + sy) * SW],
+                       &hint[((size_t)t * FH + (fy0 + sy)) * (size_t)hint_pitch + fx0], (size_t)SW);
+    }
+    int st = oracle_iterate_frame_f64(sub, 1, SH, SW, r, iters, tie, NULL, NULL, subhint, hint_thresh, n_hinted,
                                       ORACLE_STORE_NONE);
+    free(subhint);
     if (st == ORACLE_OK)
         for (int y = y0; y < y1; ++y)
             for (int x = x0; x < x1; ++x)

@@ -1,0 +1,473 @@
+// osbf_api.cu -- the C ABI of libosbf.so (see include/osbf.h): argument checks,
+// workspace, the sequence of fused-group launches, host-buffer calls, tuning.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "osbf.h"
+#include "osbf_internal.h"
+
+using namespace osbf;
+
+struct osbf_ctx {
+    int device = 0;
+    int sms = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    void *frames[2] = {nullptr, nullptr};
+    size_t frame_bytes[2] = {0, 0};
+    void *dev_in = nullptr, *dev_out = nullptr;  // osbf_filter_host staging
+    size_t dev_in_bytes = 0, dev_out_bytes = 0;
+    void *ws[4] = {nullptr, nullptr, nullptr, nullptr};  // backward / checkpoint workspaces
+    size_t ws_bytes[4] = {0, 0, 0, 0};
+    int last_launches = 0;
+    std::map<std::tuple<int, int, int>, int> tuned;  // (dtype, r, size class) -> depth
+    void *batch_state = nullptr;                     // owned by the batched launcher
+};
+
+// implemented in osbf_bwd_api.cu / osbf_batched.cu
+osbf_status osbf_backward_impl(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps, int P,
+                               int H, int W, int r, int iters, cudaStream_t s);
+void osbf_batched_free(osbf_ctx *ctx);
+
+namespace {
+
+osbf_status fail(osbf_ctx *ctx, osbf_status code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+#define OSBF_CK(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(ctx, OSBF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Runs a body with ctx->device current and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_size(osbf_dtype dt) {
+    switch (dt) {
+    case OSBF_F32: return 4;
+    case OSBF_F16: return 2;
+    case OSBF_BF16: return 2;
+    case OSBF_U8: return 1;
+    }
+    return 0;
+}
+
+Storage storage_of(osbf_dtype dt) {
+    switch (dt) {
+    case OSBF_F16: return Storage::F16;
+    case OSBF_BF16: return Storage::BF16;
+    case OSBF_U8: return Storage::U8;
+    default: return Storage::F32;
+    }
+}
+
+bool overlaps(const void *a, size_t an, const void *b, size_t bn) {
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + bn && pb < pa + an;
+}
+
+osbf_status ensure(osbf_ctx *ctx, void **slot, size_t *have, size_t need) {
+    if (*have >= need) return OSBF_OK;
+    if (*slot) cudaFree(*slot);
+    *slot = nullptr;
+    *have = 0;
+    if (cudaMalloc(slot, need) != cudaSuccess) {
+        cudaGetLastError();
+        *slot = nullptr;
+        return fail(ctx, OSBF_ENOMEM, "cudaMalloc of %zu bytes failed", need);
+    }
+    *have = need;
+    return OSBF_OK;
+}
+
+// default fused depth before tuning: small radii amortise the halo best
+int default_depth(int r, osbf_dtype dt) {
+    (void)dt;
+    if (r <= 1) return 4;
+    if (r <= 2) return 4;
+    if (r <= 4) return 2;
+    return 1;
+}
+
+int size_class(long long pixels) {
+    int c = 0;
+    while (pixels > (1LL << 20) && c < 8) {
+        pixels >>= 2;
+        ++c;
+    }
+    return c;
+}
+
+cudaError_t launch_group(Storage st, bool u8first, int R, bool tie_app, bool maps, const FwdParams &p, dim3 grid,
+                         cudaStream_t s) {
+    if (u8first) return launch_fwd_u8(R, tie_app, p, grid, s);
+    switch (st) {
+    case Storage::F16: return launch_fwd_f16(R, tie_app, maps, p, grid, s);
+    case Storage::BF16: return launch_fwd_bf16(R, tie_app, maps, p, grid, s);
+    default:
+        return tie_app ? launch_fwd_f32_appendix(R, maps, p, grid, s) : launch_fwd_f32_paper(R, maps, p, grid, s);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// the forward driver (also used by the checkpointed forward and the backward's recompute)
+// ------------------------------------------------------------------------------------
+// Runs `iters` passes.  `in` is the caller's image (in_is_frame = 0) or a padded
+// float frame (in_is_frame = 1, row pitch in_pitch); `out` is the caller's cropped
+// output (out_is_frame = 0) or a padded float frame (out_is_frame = 1, pitch out_pitch).
+osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int in_pitch, void *out, int out_is_frame,
+                             int out_pitch, int P, int H, int W, int r, int iters, osbf_dtype dtype, int depth,
+                             int tie, uint8_t *maps, int maps_iter0, long long maps_iter_stride, cudaStream_t s) {
+    const Storage st = storage_of(dtype);
+    const int FH = H + 2 * r, FW = W + 2 * r;
+    const size_t fes = dtype == OSBF_U8 ? 4 : elem_size(dtype);  // frame element size
+    const int align_el = (int)(128 / fes);
+    const int FWp = (FW + align_el - 1) / align_el * align_el;
+    const size_t frame_bytes = fes * (size_t)P * FH * FWp;
+
+    int D = depth > 0 ? depth : 0;
+    if (D == 0) {
+        auto it = ctx->tuned.find(std::make_tuple((int)dtype, r, size_class((long long)P * H * W)));
+        D = it != ctx->tuned.end() ? it->second : default_depth(r, dtype);
+    }
+    if (D > OSBF_MAX_DEPTH) D = OSBF_MAX_DEPTH;
+    while (D > 1 && fwd_smem(st, r, D) > ctx->smem_optin) --D;
+    if (fwd_smem(st, r, 1) > ctx->smem_optin) return fail(ctx, OSBF_EUNSUPPORTED, "tile does not fit shared memory");
+
+    // plan the launches
+    std::vector<int> groups;
+    int done = 0;
+    const bool u8 = dtype == OSBF_U8 && !in_is_frame;
+    if (u8) {
+        groups.push_back(1);
+        done = 1;
+    }
+    while (done < iters) {
+        const int g = iters - done < D ? iters - done : D;
+        groups.push_back(g);
+        done += g;
+    }
+    const int nl = (int)groups.size();
+    const bool final_to_frame = out_is_frame != 0;
+    if (nl >= 2) {
+        osbf_status e = ensure(ctx, &ctx->frames[0], &ctx->frame_bytes[0], frame_bytes);
+        if (e) return e;
+    }
+    if (nl >= 3) {
+        osbf_status e = ensure(ctx, &ctx->frames[1], &ctx->frame_bytes[1], frame_bytes);
+        if (e) return e;
+    }
+
+    const void *src = in;
+    int src_is_input = in_is_frame ? 0 : 1;
+    long long src_plane = in_is_frame ? (long long)FH * in_pitch : (long long)H * W;
+    int src_pitch = in_is_frame ? in_pitch : W;
+    int passes = 0;
+    for (int g = 0; g < nl; ++g) {
+        const bool last = g == nl - 1;
+        FwdParams p;
+        std::memset(&p, 0, sizeof p);
+        p.src = src;
+        p.src_is_input = src_is_input;
+        p.src_plane = src_plane;
+        p.src_pitch = src_pitch;
+        p.H = H;
+        p.W = W;
+        p.FH = FH;
+        p.FW = FW;
+        p.D = groups[g];
+        p.maps = maps;
+        p.map_iter0 = maps_iter0 + passes;
+        p.map_iter_stride = maps_iter_stride;
+        p.map_plane = (long long)FH * FW;
+        if (last && !final_to_frame) {
+            p.dst = out;
+            p.dst_is_output = 1;
+            p.dst_plane = (long long)H * W;
+            p.dst_pitch = W;
+        } else if (last) {
+            p.dst = out;
+            p.dst_is_output = 0;
+            p.dst_plane = (long long)FH * out_pitch;
+            p.dst_pitch = out_pitch;
+        } else {
+            p.dst = ctx->frames[g & 1];
+            p.dst_is_output = 0;
+            p.dst_plane = (long long)FH * FWp;
+            p.dst_pitch = FWp;
+        }
+        int ty0 = 0, ty1 = (FH - 1) / kTH, tx0 = 0, tx1 = (FW - 1) / kTW;
+        if (p.dst_is_output && !maps) {  // with maps, every frame pixel's selection is recorded
+            ty0 = r / kTH;
+            ty1 = (r + H - 1) / kTH;
+            tx0 = r / kTW;
+            tx1 = (r + W - 1) / kTW;
+        }
+        p.ty_off = ty0;
+        p.tx_off = tx0;
+        const bool u8first = u8 && g == 0;
+        // planes go in grid.z; split if there are more than the grid allows
+        for (int p0 = 0; p0 < P; p0 += 65535) {
+            const int np = P - p0 < 65535 ? P - p0 : 65535;
+            FwdParams q = p;
+            const size_t ses = (u8first ? 1 : (src_is_input ? elem_size(dtype) : fes));
+            const size_t des = p.dst_is_output ? (dtype == OSBF_U8 ? 4 : elem_size(dtype)) : fes;
+            q.src = (const char *)p.src + ses * (size_t)p0 * p.src_plane;
+            q.dst = (char *)p.dst + des * (size_t)p0 * p.dst_plane;
+            if (q.maps) q.maps = p.maps + (size_t)p0 * p.map_plane;
+            dim3 grid(tx1 - tx0 + 1, ty1 - ty0 + 1, np);
+            cudaError_t e = launch_group(st, u8first, r, tie != 0, maps != nullptr, q, grid, s);
+            if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "forward launch failed: %s", cudaGetErrorString(e));
+            ctx->last_launches += 1;
+        }
+        passes += groups[g];
+        src = p.dst;
+        src_is_input = 0;
+        src_plane = p.dst_plane;
+        src_pitch = p.dst_pitch;
+    }
+    return OSBF_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+const char *osbf_version(void) { return "osbf-gb300 0.1 (sm_103a)"; }
+
+osbf_status osbf_create(osbf_ctx **out, int device) {
+    if (!out) return OSBF_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return device < 0 ? OSBF_EINVAL : OSBF_ECUDA;
+    }
+    osbf_ctx *ctx = new (std::nothrow) osbf_ctx();
+    if (!ctx) return OSBF_ENOMEM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    ctx->sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    ctx->smem_optin = (size_t)v;
+    *out = ctx;
+    return OSBF_OK;
+}
+
+void osbf_destroy(osbf_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (void *p : ctx->frames)
+        if (p) cudaFree(p);
+    for (void *p : ctx->ws)
+        if (p) cudaFree(p);
+    if (ctx->dev_in) cudaFree(ctx->dev_in);
+    if (ctx->dev_out) cudaFree(ctx->dev_out);
+    osbf_batched_free(ctx);
+    delete ctx;
+}
+
+const char *osbf_last_error(const osbf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int osbf_last_launch_count(const osbf_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
+                           osbf_dtype dtype, const osbf_options *opts, void *stream) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->err.clear();
+    ctx->last_launches = 0;
+    if (!in || !out) return fail(ctx, OSBF_EINVAL, "null image pointer");
+    if (N <= 0 || C <= 0 || H <= 0 || W <= 0) return fail(ctx, OSBF_EINVAL, "N, C, H and W must be positive");
+    if (r < 0 || iters < 0) return fail(ctx, OSBF_EINVAL, "r and iters must be >= 0");
+    if (dtype < OSBF_F32 || dtype > OSBF_U8) return fail(ctx, OSBF_EINVAL, "unknown dtype %d", (int)dtype);
+    osbf_options o;
+    std::memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    if (o.depth < 0 || o.depth > OSBF_MAX_DEPTH) return fail(ctx, OSBF_EINVAL, "depth must be in 0..%d", OSBF_MAX_DEPTH);
+    if (o.tie != OSBF_TIE_PAPER && o.tie != OSBF_TIE_APPENDIX) return fail(ctx, OSBF_EINVAL, "unknown tie order");
+    for (int v : o.reserved)
+        if (v) return fail(ctx, OSBF_EINVAL, "reserved option fields must be zero");
+    if (r > OSBF_MAX_RADIUS) return fail(ctx, OSBF_EUNSUPPORTED, "r = %d exceeds OSBF_MAX_RADIUS = %d", r, OSBF_MAX_RADIUS);
+    if (o.maps && (dtype == OSBF_F16 || dtype == OSBF_BF16) && o.tie != OSBF_TIE_PAPER)
+        return fail(ctx, OSBF_EUNSUPPORTED, "16-bit storage keeps selection maps with the paper tie order only");
+    const long long P = (long long)N * C;
+    if (P * H * (long long)W > (1LL << 40)) return fail(ctx, OSBF_EUNSUPPORTED, "image too large");
+    const size_t in_bytes = elem_size(dtype) * (size_t)P * H * W;
+    const size_t out_bytes = (dtype == OSBF_U8 ? 4 : elem_size(dtype)) * (size_t)P * H * W;
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(ctx, OSBF_EINVAL, "in and out overlap");
+    const int FH = H + 2 * r, FW = W + 2 * r;
+    const long long map_stride = P * FH * FW;
+    if (o.maps && iters > 0 && (overlaps(o.maps, (size_t)map_stride * iters, in, in_bytes) ||
+                                overlaps(o.maps, (size_t)map_stride * iters, out, out_bytes)))
+        return fail(ctx, OSBF_EINVAL, "maps overlap an image");
+
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r == 0 || iters == 0) {
+        // every window is the centre pixel (r = 0) or no pass runs: the input itself
+        if (dtype == OSBF_U8) {
+            OSBF_CK(launch_u8_to_f32((const uint8_t *)in, (float *)out, P * H * W, s));
+        } else {
+            OSBF_CK(cudaMemcpyAsync(out, in, in_bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        ctx->last_launches = 1;
+        if (o.maps && iters > 0) {
+            // all |d_i| are 0: the first window of the tie order is selected everywhere
+            const uint8_t first = o.tie == OSBF_TIE_APPENDIX ? 6 : 1;
+            OSBF_CK(launch_fill_u8(o.maps, first, map_stride * iters, s));
+            ctx->last_launches += 1;
+        }
+        return OSBF_OK;
+    }
+    return osbf_forward_run(ctx, in, 0, 0, out, 0, 0, (int)P, H, W, r, iters, dtype, o.depth, o.tie, o.maps, 0,
+                            map_stride, s);
+}
+
+osbf_status osbf_filter(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
+                        osbf_dtype dtype, void *stream) {
+    return osbf_filter_ex(ctx, in, out, N, C, H, W, r, iters, dtype, nullptr, stream);
+}
+
+osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
+                             osbf_dtype dtype, void *stream) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->err.clear();
+    if (!in || !out) return fail(ctx, OSBF_EINVAL, "null image pointer");
+    if (N <= 0 || C <= 0 || H <= 0 || W <= 0) return fail(ctx, OSBF_EINVAL, "N, C, H and W must be positive");
+    if (dtype < OSBF_F32 || dtype > OSBF_U8) return fail(ctx, OSBF_EINVAL, "unknown dtype %d", (int)dtype);
+    const long long P = (long long)N * C;
+    const size_t in_bytes = elem_size(dtype) * (size_t)P * H * W;
+    const size_t out_bytes = (dtype == OSBF_U8 ? 4 : elem_size(dtype)) * (size_t)P * H * W;
+    DeviceGuard g(ctx->device);
+    osbf_status e = ensure(ctx, &ctx->dev_in, &ctx->dev_in_bytes, in_bytes);
+    if (e) return e;
+    e = ensure(ctx, &ctx->dev_out, &ctx->dev_out_bytes, out_bytes);
+    if (e) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    OSBF_CK(cudaMemcpyAsync(ctx->dev_in, in, in_bytes, cudaMemcpyHostToDevice, s));
+    e = osbf_filter_ex(ctx, ctx->dev_in, ctx->dev_out, N, C, H, W, r, iters, dtype, nullptr, stream);
+    if (e) return e;
+    OSBF_CK(cudaMemcpyAsync(out, ctx->dev_out, out_bytes, cudaMemcpyDeviceToHost, s));
+    OSBF_CK(cudaStreamSynchronize(s));
+    return OSBF_OK;
+}
+
+osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int iters) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->err.clear();
+    if (planes <= 0 || H <= 0 || W <= 0 || r < 1 || iters < 1) return fail(ctx, OSBF_EINVAL, "bad tuning problem");
+    if (r > OSBF_MAX_RADIUS) return fail(ctx, OSBF_EUNSUPPORTED, "r exceeds OSBF_MAX_RADIUS");
+    if (dtype < OSBF_F32 || dtype > OSBF_U8) return fail(ctx, OSBF_EINVAL, "unknown dtype");
+    DeviceGuard g(ctx->device);
+    const size_t in_bytes = elem_size(dtype) * (size_t)planes * H * W;
+    const size_t out_bytes = (dtype == OSBF_U8 ? 4 : elem_size(dtype)) * (size_t)planes * H * W;
+    void *din = nullptr, *dout = nullptr;
+    if (cudaMalloc(&din, in_bytes) != cudaSuccess || cudaMalloc(&dout, out_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (din) cudaFree(din);
+        return fail(ctx, OSBF_ENOMEM, "tuning buffers");
+    }
+    cudaMemset(din, 0, in_bytes);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const Storage st = storage_of(dtype);
+    int best_d = 1;
+    float best_ms = 1e30f;
+    osbf_status status = OSBF_OK;
+    for (int D = 1; D <= OSBF_MAX_DEPTH; ++D) {
+        if (D > iters || fwd_smem(st, r, D) > ctx->smem_optin) break;
+        osbf_options o;
+        std::memset(&o, 0, sizeof o);
+        o.depth = D;
+        status = osbf_filter_ex(ctx, din, dout, planes, 1, H, W, r, iters, dtype, &o, s);  // warm-up
+        if (status) break;
+        cudaEventRecord(e0, s);
+        const int reps = 3;
+        for (int k = 0; k < reps && !status; ++k)
+            status = osbf_filter_ex(ctx, din, dout, planes, 1, H, W, r, iters, dtype, &o, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (status) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_d = D;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(din);
+    cudaFree(dout);
+    if (status) return status;
+    ctx->tuned[std::make_tuple((int)dtype, r, size_class((long long)planes * H * W))] = best_d;
+    return OSBF_OK;
+}
+
+osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps, int N,
+                                 int C, int H, int W, int r, int iters, void *stream) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->err.clear();
+    ctx->last_launches = 0;
+    if (!grad_out || !grad_in || (!maps && iters > 0 && r > 0)) return fail(ctx, OSBF_EINVAL, "null pointer");
+    if (N <= 0 || C <= 0 || H <= 0 || W <= 0) return fail(ctx, OSBF_EINVAL, "N, C, H and W must be positive");
+    if (r < 0 || iters < 0) return fail(ctx, OSBF_EINVAL, "r and iters must be >= 0");
+    if (r > OSBF_MAX_RADIUS) return fail(ctx, OSBF_EUNSUPPORTED, "r exceeds OSBF_MAX_RADIUS");
+    const long long P = (long long)N * C;
+    const size_t bytes = 4 * (size_t)P * H * W;
+    if (overlaps(grad_out, bytes, grad_in, bytes)) return fail(ctx, OSBF_EINVAL, "grad_out and grad_in overlap");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r == 0 || iters == 0) {
+        OSBF_CK(cudaMemcpyAsync(grad_in, grad_out, bytes, cudaMemcpyDeviceToDevice, s));
+        ctx->last_launches = 1;
+        return OSBF_OK;
+    }
+    return osbf_backward_impl(ctx, grad_out, grad_in, maps, (int)P, H, W, r, iters, s);
+}
+
+}  // extern "C"
+
+// accessors for the other translation units
+void *osbf_ctx_workspace(osbf_ctx *ctx, int slot, size_t bytes, osbf_status *st) {
+    *st = ensure(ctx, &ctx->ws[slot], &ctx->ws_bytes[slot], bytes);
+    return *st == OSBF_OK ? ctx->ws[slot] : nullptr;
+}
+osbf_status osbf_ctx_fail(osbf_ctx *ctx, osbf_status code, const char *msg) { return fail(ctx, code, "%s", msg); }
+void osbf_ctx_count_launches(osbf_ctx *ctx, int n) { ctx->last_launches += n; }
+int osbf_ctx_sms(const osbf_ctx *ctx) { return ctx->sms; }
+int osbf_ctx_device(const osbf_ctx *ctx) { return ctx->device; }
+void **osbf_ctx_batch_state(osbf_ctx *ctx) { return &ctx->batch_state; }

@@ -1,0 +1,41 @@
+// Small elementwise kernels of the library (type conversion, fills).
+#include "osbf_internal.h"
+
+namespace osbf {
+
+__global__ void u8_to_f32_kernel(const uint8_t *__restrict__ in, float *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+__global__ void fill_u8_kernel(uint8_t *__restrict__ p, uint8_t v, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+static int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    return (int)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
+}
+
+cudaError_t launch_u8_to_f32(const uint8_t *in, float *out, long long n, cudaStream_t s) {
+    u8_to_f32_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u8(uint8_t *p, uint8_t v, long long n, cudaStream_t s) {
+    fill_u8_kernel<<<grid_for(n), 256, 0, s>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+size_t fwd_smem(Storage st, int R, int D) {
+    switch (st) {
+    case Storage::F32: return fwd_smem_bytes<float, float>(R, D);
+    case Storage::F16: return fwd_smem_bytes<__half, __half>(R, D);
+    case Storage::BF16: return fwd_smem_bytes<__nv_bfloat16, __nv_bfloat16>(R, D);
+    case Storage::U8: return fwd_smem_bytes<uint8_t, float>(R, D);
+    }
+    return 0;
+}
+
+}  // namespace osbf

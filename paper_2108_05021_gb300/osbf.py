@@ -1,0 +1,301 @@
+"""Python binding of libosbf.so (the C ABI in include/osbf.h).
+
+Argument marshalling only: every pass of the filter runs in the library's CUDA
+kernels.  Tensors must be CUDA tensors, contiguous, in NCHW (H x W and P x H x W
+are accepted as N = C = 1 and N = 1).  Work is enqueued on the current torch
+stream of the tensor's device.  If the library is not built, every call raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libosbf.so")
+
+OSBF_MAX_RADIUS = 16
+OSBF_MAX_DEPTH = 8
+_STATUS = {0: "OSBF_OK", 1: "OSBF_EINVAL", 2: "OSBF_ENOMEM", 3: "OSBF_ECUDA", 4: "OSBF_EUNSUPPORTED",
+           5: "OSBF_ETIMEOUT"}
+_DTYPE = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2, torch.uint8: 3}
+_TIE = {"paper": 0, "appendix": 1}
+
+
+class OSBFError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.status_name = _STATUS.get(status, str(status))
+        super().__init__(f"{self.status_name}: {message}")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("tie", ctypes.c_int), ("maps", ctypes.c_void_p),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("r", ctypes.c_int), ("iters", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_ctxs: dict[int, ctypes.c_void_p] = {}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library.  Raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libosbf.so is not built ({LIB_PATH}); run paper_2108_05021_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+        L.osbf_create.argtypes = [ctypes.POINTER(vp), i]
+        L.osbf_create.restype = st
+        L.osbf_destroy.argtypes = [vp]
+        L.osbf_destroy.restype = None
+        L.osbf_last_error.argtypes = [vp]
+        L.osbf_last_error.restype = ctypes.c_char_p
+        L.osbf_last_launch_count.argtypes = [vp]
+        L.osbf_last_launch_count.restype = i
+        L.osbf_version.restype = ctypes.c_char_p
+        L.osbf_filter.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, vp]
+        L.osbf_filter.restype = st
+        L.osbf_filter_ex.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, ctypes.POINTER(_Options), vp]
+        L.osbf_filter_ex.restype = st
+        L.osbf_filter_host.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, vp]
+        L.osbf_filter_host.restype = st
+        L.osbf_filter_backward.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
+        L.osbf_filter_backward.restype = st
+        L.osbf_filter_checkpointed.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, i, vp]
+        L.osbf_filter_checkpointed.restype = st
+        L.osbf_filter_backward_checkpointed.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, i, vp]
+        L.osbf_filter_backward_checkpointed.restype = st
+        L.osbf_filter_batched.argtypes = [vp, ctypes.POINTER(_Job), i, vp]
+        L.osbf_filter_batched.restype = st
+        L.osbf_autotune.argtypes = [vp, i, i, i, i, i, i]
+        L.osbf_autotune.restype = st
+        _lib = L
+    return _lib
+
+
+def _destroy_all():
+    if _lib is None:
+        return
+    for c in list(_ctxs.values()):
+        _lib.osbf_destroy(c)
+    _ctxs.clear()
+
+
+atexit.register(_destroy_all)
+
+
+def context(device: int) -> ctypes.c_void_p:
+    """The library context of a CUDA device (created on first use, kept until exit)."""
+    with _lock:
+        c = _ctxs.get(device)
+        if c is None:
+            c = ctypes.c_void_p()
+            st = lib().osbf_create(ctypes.byref(c), device)
+            if st != 0:
+                raise OSBFError(st, f"osbf_create(device={device}) failed")
+            _ctxs[device] = c
+        return c
+
+
+def _check(st: int, ctx: ctypes.c_void_p):
+    if st != 0:
+        msg = lib().osbf_last_error(ctx)
+        raise OSBFError(st, msg.decode() if msg else "")
+
+
+def _stream(device: int) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _nchw(x: torch.Tensor):
+    if x.dim() == 2:
+        return 1, 1, x.shape[0], x.shape[1]
+    if x.dim() == 3:
+        return 1, x.shape[0], x.shape[1], x.shape[2]
+    if x.dim() == 4:
+        return tuple(x.shape)
+    raise ValueError("expected an H x W, P x H x W or N x C x H x W tensor")
+
+
+def _require_cuda(*ts: torch.Tensor):
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("the library works on CUDA tensors only (use filter_host for host buffers)")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def version() -> str:
+    return lib().osbf_version().decode()
+
+
+def last_launch_count(device: int = 0) -> int:
+    """Kernel launches enqueued by the last filter call on this device's context."""
+    return lib().osbf_last_launch_count(context(device))
+
+
+def maps_shape(x: torch.Tensor, r: int, iters: int):
+    N, C, H, W = _nchw(x)
+    return (iters, N * C, H + 2 * r, W + 2 * r)
+
+
+def filter(x: torch.Tensor, r: int, iters: int, *, depth: int = 0, tie: str = "paper",
+           maps: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Forward One-Sided Box Filter (osbf_filter_ex).  uint8 input gives float32 output."""
+    _require_cuda(x)
+    N, C, H, W = _nchw(x)
+    if x.dtype not in _DTYPE:
+        raise TypeError(f"unsupported dtype {x.dtype}")
+    odt = torch.float32 if x.dtype == torch.uint8 else x.dtype
+    if out is None:
+        out = torch.empty(x.shape, dtype=odt, device=x.device)
+    _require_cuda(out)
+    if out.dtype != odt or out.shape != x.shape:
+        raise ValueError("out has the wrong dtype or shape")
+    opts = _Options(depth, _TIE[tie], None, (ctypes.c_int * 4)())
+    if maps is not None:
+        _require_cuda(maps)
+        if maps.dtype != torch.uint8 or tuple(maps.shape) != maps_shape(x, r, iters):
+            raise ValueError(f"maps must be uint8 of shape {maps_shape(x, r, iters)}")
+        opts.maps = maps.data_ptr()
+    dev = x.device.index
+    ctx = context(dev)
+    _check(lib().osbf_filter_ex(ctx, x.data_ptr(), out.data_ptr(), N, C, H, W, r, iters, _DTYPE[x.dtype],
+                                ctypes.byref(opts), _stream(dev)), ctx)
+    return out
+
+
+def filter_host(x: torch.Tensor, r: int, iters: int, *, out: Optional[torch.Tensor] = None,
+                device: int = 0) -> torch.Tensor:
+    """osbf_filter_host: host (ideally pinned) input and output; returns once `out` is filled."""
+    if x.is_cuda or not x.is_contiguous():
+        raise ValueError("filter_host takes a contiguous host tensor")
+    N, C, H, W = _nchw(x)
+    odt = torch.float32 if x.dtype == torch.uint8 else x.dtype
+    if out is None:
+        out = torch.empty(x.shape, dtype=odt, pin_memory=x.is_pinned())
+    ctx = context(device)
+    with torch.cuda.device(device):
+        _check(lib().osbf_filter_host(ctx, x.data_ptr(), out.data_ptr(), N, C, H, W, r, iters, _DTYPE[x.dtype],
+                                      _stream(device)), ctx)
+    return out
+
+
+def backward(grad_out: torch.Tensor, maps: torch.Tensor, r: int, iters: int,
+             out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """osbf_filter_backward: vector-Jacobian product with the selections frozen to `maps`."""
+    _require_cuda(grad_out, maps)
+    if grad_out.dtype != torch.float32:
+        raise TypeError("grad_out must be float32")
+    N, C, H, W = _nchw(grad_out)
+    if out is None:
+        out = torch.empty_like(grad_out)
+    dev = grad_out.device.index
+    ctx = context(dev)
+    _check(lib().osbf_filter_backward(ctx, grad_out.data_ptr(), out.data_ptr(), maps.data_ptr(), N, C, H, W, r,
+                                      iters, _stream(dev)), ctx)
+    return out
+
+
+def checkpoint_count(iters: int, interval: int) -> int:
+    return (iters + interval - 1) // interval
+
+
+def filter_checkpointed(x: torch.Tensor, r: int, iters: int, interval: int):
+    """Forward that keeps a padded frame every `interval` passes; returns (out, checkpoints)."""
+    _require_cuda(x)
+    N, C, H, W = _nchw(x)
+    ck = torch.empty((checkpoint_count(iters, interval), N * C, H + 2 * r, W + 2 * r), dtype=torch.float32,
+                     device=x.device)
+    out = torch.empty_like(x)
+    dev = x.device.index
+    ctx = context(dev)
+    _check(lib().osbf_filter_checkpointed(ctx, x.data_ptr(), out.data_ptr(), ck.data_ptr(), interval, N, C, H, W, r,
+                                          iters, _stream(dev)), ctx)
+    return out, ck
+
+
+def backward_checkpointed(grad_out: torch.Tensor, checkpoints: torch.Tensor, r: int, iters: int,
+                          interval: int) -> torch.Tensor:
+    _require_cuda(grad_out, checkpoints)
+    N, C, H, W = _nchw(grad_out)
+    out = torch.empty_like(grad_out)
+    dev = grad_out.device.index
+    ctx = context(dev)
+    _check(lib().osbf_filter_backward_checkpointed(ctx, grad_out.data_ptr(), out.data_ptr(), checkpoints.data_ptr(),
+                                                   interval, N, C, H, W, r, iters, _stream(dev)), ctx)
+    return out
+
+
+def batched(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequence[int],
+            outputs: Optional[Sequence[torch.Tensor]] = None) -> list:
+    """osbf_filter_batched: many H x W float32 images of different sizes, radii and pass counts."""
+    n = len(inputs)
+    if outputs is None:
+        outputs = [torch.empty_like(t) for t in inputs]
+    jobs = (_Job * n)()
+    dev = None
+    for k, (t, o, r, it) in enumerate(zip(inputs, outputs, radii, iters)):
+        _require_cuda(t, o)
+        if t.dim() != 2 or t.dtype != torch.float32 or o.shape != t.shape or o.dtype != t.dtype:
+            raise ValueError("batched jobs are H x W float32 images")
+        dev = t.device.index if dev is None else dev
+        jobs[k] = _Job(t.data_ptr(), o.data_ptr(), t.shape[0], t.shape[1], int(r), int(it))
+    dev = 0 if dev is None else dev
+    ctx = context(dev)
+    _check(lib().osbf_filter_batched(ctx, jobs, n, _stream(dev)), ctx)
+    return list(outputs)
+
+
+def autotune(dtype: torch.dtype, planes: int, H: int, W: int, r: int, iters: int, device: int = 0) -> None:
+    ctx = context(device)
+    with torch.cuda.device(device):
+        _check(lib().osbf_autotune(ctx, _DTYPE[dtype], planes, H, W, r, iters), ctx)
+
+
+class OSBFFunction(torch.autograd.Function):
+    """Autograd wrapper: forward keeps every pass's selection map (1 byte per frame
+    pixel and pass) or, with `checkpoint_interval`, a frame every that many passes;
+    backward is the library's adjoint kernel (selection treated as constant)."""
+
+    @staticmethod
+    def forward(ctx, x, r: int, iters: int, checkpoint_interval: int = 0):
+        if checkpoint_interval and checkpoint_interval > 0:
+            out, ck = filter_checkpointed(x.contiguous(), r, iters, checkpoint_interval)
+            ctx.save_for_backward(ck)
+            ctx.mode = "checkpoint"
+        else:
+            maps = torch.empty(maps_shape(x, r, iters), dtype=torch.uint8, device=x.device)
+            out = filter(x.contiguous(), r, iters, maps=maps)
+            ctx.save_for_backward(maps)
+            ctx.mode = "maps"
+        ctx.r, ctx.iters, ctx.interval = r, iters, checkpoint_interval
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        (saved,) = ctx.saved_tensors
+        g = g.contiguous()
+        if ctx.mode == "maps":
+            gi = backward(g, saved, ctx.r, ctx.iters)
+        else:
+            gi = backward_checkpointed(g, saved, ctx.r, ctx.iters, ctx.interval)
+        return gi, None, None, None
+
+
+def osbf(x: torch.Tensor, r: int, iters: int, checkpoint_interval: int = 0) -> torch.Tensor:
+    """Differentiable One-Sided Box Filter on float32 CUDA tensors."""
+    return OSBFFunction.apply(x, r, iters, checkpoint_interval)
