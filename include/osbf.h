@@ -160,6 +160,11 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
  * candidates on the device (synchronous); later calls with depth 0 use it. */
 osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int iters);
 
+/* Synchronise the context's device and report whether any kernel of this context
+ * gave up a bounded device-side wait since the last check (OSBF_ETIMEOUT; the
+ * outputs of that call are undefined), then clear the record.  OSBF_OK otherwise. */
+osbf_status osbf_check(osbf_ctx *ctx);
+
 /* Number of kernel launches the last filter call on `ctx` enqueued. */
 int osbf_last_launch_count(const osbf_ctx *ctx);
 

@@ -27,6 +27,7 @@ struct osbf_ctx {
     int last_launches = 0;
     std::map<std::tuple<int, int, int>, int> tuned;  // (dtype, r, size class) -> depth
     void *batch_state = nullptr;                     // owned by the batched launcher
+    unsigned int *err_word = nullptr;                // device: bit 0 = a bounded device wait gave up
 };
 
 // implemented in osbf_bwd_api.cu / osbf_batched.cu
@@ -123,31 +124,65 @@ int size_class(long long pixels) {
     return c;
 }
 
-cudaError_t launch_group(Storage st, bool u8first, int R, bool tie_app, bool maps, const FwdParams &p, dim3 grid,
-                         cudaStream_t s) {
-    if (u8first) return launch_fwd_u8(R, tie_app, p, grid, s);
-    switch (st) {
-    case Storage::F16: return launch_fwd_f16(R, tie_app, maps, p, grid, s);
-    case Storage::BF16: return launch_fwd_bf16(R, tie_app, maps, p, grid, s);
-    default:
-        return tie_app ? launch_fwd_f32_appendix(R, maps, p, grid, s) : launch_fwd_f32_paper(R, maps, p, grid, s);
-    }
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------------------------
 // the forward driver (also used by the checkpointed forward and the backward's recompute)
 // ------------------------------------------------------------------------------------
-// Runs `iters` passes.  `in` is the caller's image (in_is_frame = 0) or a padded
-// float frame (in_is_frame = 1, row pitch in_pitch); `out` is the caller's cropped
-// output (out_is_frame = 0) or a padded float frame (out_is_frame = 1, pitch out_pitch).
+namespace {
+
+struct V2Plan {
+    int D;
+    size_t smem;
+};
+
+size_t smem_v2(Storage st, int r, int D, bool direct = false) {
+    switch (st) {
+    case Storage::F16: return smem_fwd2_f16(r, D, direct);
+    case Storage::BF16: return smem_fwd2_bf16(r, D, direct);
+    default: return smem_fwd2_f32(r, D, direct);
+    }
+}
+
+int occupancy_v2(Storage st, int r, bool tie_app, bool maps, bool direct, int D) {
+    switch (st) {
+    case Storage::F16: return occupancy_fwd2_f16(r, tie_app, maps, direct, D);
+    case Storage::BF16: return occupancy_fwd2_bf16(r, tie_app, maps, direct, D);
+    default: return occupancy_fwd2_f32(r, tie_app, maps, direct, D);
+    }
+}
+
+cudaError_t launch_v2(Storage st, int r, bool tie_app, bool maps, bool direct, const CUtensorMap &m,
+                      const v2::Fwd2Params &p, int grid, cudaStream_t s) {
+    switch (st) {
+    case Storage::F16: return launch_fwd2_f16(r, tie_app, maps, direct, m, p, grid, s);
+    case Storage::BF16: return launch_fwd2_bf16(r, tie_app, maps, direct, m, p, grid, s);
+    default: return launch_fwd2_f32(r, tie_app, maps, direct, m, p, grid, s);
+    }
+}
+
+// largest fused depth <= D whose tile fits shared memory and the TMA box limits
+int fit_depth(osbf_ctx *ctx, Storage st, int r, int D) {
+    for (; D > 1; --D) {
+        const int e = D * r;
+        const int rw0 = v2::TW + 2 * round_up(e, st == Storage::F32 ? 4 : 8);
+        if (smem_v2(st, r, D) <= ctx->smem_optin && rw0 + 16 <= 256 && v2::TH + 2 * e <= 256) break;
+    }
+    return D;
+}
+
+}  // namespace
+
+// Runs `iters` passes.  `in` is the caller's image (in_is_frame = 0) or a padded frame
+// of the storage type (in_is_frame = 1, row pitch in_pitch elements); `out` is the
+// caller's cropped output (out_is_frame = 0) or a padded frame (pitch out_pitch).
 osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int in_pitch, void *out, int out_is_frame,
                              int out_pitch, int P, int H, int W, int r, int iters, osbf_dtype dtype, int depth,
                              int tie, uint8_t *maps, int maps_iter0, long long maps_iter_stride, cudaStream_t s) {
-    const Storage st = storage_of(dtype);
+    // 8-bit input: the exact first pass writes a float32 frame; later passes run in float32
+    const Storage st = dtype == OSBF_U8 ? Storage::F32 : storage_of(dtype);
     const int FH = H + 2 * r, FW = W + 2 * r;
-    const size_t fes = dtype == OSBF_U8 ? 4 : elem_size(dtype);  // frame element size
+    const size_t fes = st == Storage::F32 ? 4 : 2;  // frame element size
     const int align_el = (int)(128 / fes);
     const int FWp = (FW + align_el - 1) / align_el * align_el;
     const size_t frame_bytes = fes * (size_t)P * FH * FWp;
@@ -158,100 +193,153 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         D = it != ctx->tuned.end() ? it->second : default_depth(r, dtype);
     }
     if (D > OSBF_MAX_DEPTH) D = OSBF_MAX_DEPTH;
-    while (D > 1 && fwd_smem(st, r, D) > ctx->smem_optin) --D;
-    if (fwd_smem(st, r, 1) > ctx->smem_optin) return fail(ctx, OSBF_EUNSUPPORTED, "tile does not fit shared memory");
+    D = fit_depth(ctx, st, r, D);
+    if (smem_v2(st, r, 1) > ctx->smem_optin) return fail(ctx, OSBF_EUNSUPPORTED, "tile does not fit shared memory");
 
-    // plan the launches
-    std::vector<int> groups;
-    int done = 0;
-    const bool u8 = dtype == OSBF_U8 && !in_is_frame;
-    if (u8) {
-        groups.push_back(1);
-        done = 1;
-    }
-    while (done < iters) {
-        const int g = iters - done < D ? iters - done : D;
-        groups.push_back(g);
-        done += g;
-    }
-    const int nl = (int)groups.size();
-    const bool final_to_frame = out_is_frame != 0;
-    if (nl >= 2) {
-        osbf_status e = ensure(ctx, &ctx->frames[0], &ctx->frame_bytes[0], frame_bytes);
-        if (e) return e;
-    }
-    if (nl >= 3) {
-        osbf_status e = ensure(ctx, &ctx->frames[1], &ctx->frame_bytes[1], frame_bytes);
-        if (e) return e;
-    }
+    // frame buffers: the padded input and the ping-pong targets
+    void *fb[2] = {nullptr, nullptr};
+    auto frame = [&](int k) -> void * {
+        if (!fb[k]) {
+            if (ensure(ctx, &ctx->frames[k], &ctx->frame_bytes[k], frame_bytes)) return nullptr;
+            fb[k] = ctx->frames[k];
+        }
+        return fb[k];
+    };
 
     const void *src = in;
-    int src_is_input = in_is_frame ? 0 : 1;
-    long long src_plane = in_is_frame ? (long long)FH * in_pitch : (long long)H * W;
-    int src_pitch = in_is_frame ? in_pitch : W;
+    int src_pitch = in_pitch;
+    int cur = -1;  // index of the frame buffer holding the current state (-1: the caller's)
     int passes = 0;
-    for (int g = 0; g < nl; ++g) {
-        const bool last = g == nl - 1;
-        FwdParams p;
+    if (!in_is_frame) {
+        if (dtype == OSBF_U8) {
+            // exact integer first pass (plain loads with replicate padding) into a float frame
+            const bool direct = iters == 1 && !out_is_frame;
+            FwdParams q;
+            std::memset(&q, 0, sizeof q);
+            q.src = in;
+            q.src_is_input = 1;
+            q.src_plane = (long long)H * W;
+            q.src_pitch = W;
+            q.H = H;
+            q.W = W;
+            q.FH = FH;
+            q.FW = FW;
+            q.D = 1;
+            q.maps = maps;
+            q.map_iter0 = maps_iter0;
+            q.map_iter_stride = maps_iter_stride;
+            q.map_plane = (long long)FH * FW;
+            void *dst = direct ? out : (iters == 1 ? out : frame(0));
+            if (!dst) return OSBF_ENOMEM;
+            q.dst = dst;
+            q.dst_is_output = direct ? 1 : 0;
+            q.dst_plane = direct ? (long long)H * W : (long long)FH * (iters == 1 ? out_pitch : FWp);
+            q.dst_pitch = direct ? W : (iters == 1 ? out_pitch : FWp);
+            int ty0 = 0, ty1 = (FH - 1) / kTH, tx0 = 0, tx1 = (FW - 1) / kTW;
+            if (direct && !maps) {
+                ty0 = r / kTH;
+                ty1 = (r + H - 1) / kTH;
+                tx0 = r / kTW;
+                tx1 = (r + W - 1) / kTW;
+            }
+            q.ty_off = ty0;
+            q.tx_off = tx0;
+            for (int p0 = 0; p0 < P; p0 += 65535) {
+                const int np = P - p0 < 65535 ? P - p0 : 65535;
+                FwdParams qq = q;
+                qq.src = (const uint8_t *)q.src + (size_t)p0 * q.src_plane;
+                qq.dst = (float *)q.dst + (size_t)p0 * q.dst_plane;
+                if (qq.maps) qq.maps = q.maps + (size_t)p0 * q.map_plane;
+                cudaError_t e = launch_fwd_u8(r, tie != 0, qq, dim3(tx1 - tx0 + 1, ty1 - ty0 + 1, np), s);
+                if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "first-pass launch failed: %s", cudaGetErrorString(e));
+                ctx->last_launches += 1;
+            }
+            passes = 1;
+            if (iters == 1) return OSBF_OK;
+            cur = 0;
+            src = fb[0];
+            src_pitch = FWp;
+        } else {
+            void *f0 = frame(0);
+            if (!f0) return OSBF_ENOMEM;
+            cudaError_t e = launch_pad_replicate(st, in, f0, P, H, W, r, FH, FW, FWp, s);
+            if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "pad launch failed: %s", cudaGetErrorString(e));
+            ctx->last_launches += 1;
+            cur = 0;
+            src = f0;
+            src_pitch = FWp;
+        }
+    }
+
+    while (passes < iters) {
+        const int Dg = iters - passes < D ? iters - passes : D;
+        const bool last = passes + Dg == iters;
+        const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg)
+                              : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg)
+                                                   : v2::make_layout2<__nv_bfloat16>(r, Dg);
+        CUtensorMap map;
+        if (!encode_frame_map(&map, st, src, FW, FH, P, src_pitch, L.BX, L.RH0))
+            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame %dx%dx%d, pitch %d)", FW, FH, P,
+                        src_pitch);
+        v2::Fwd2Params p;
         std::memset(&p, 0, sizeof p);
-        p.src = src;
-        p.src_is_input = src_is_input;
-        p.src_plane = src_plane;
-        p.src_pitch = src_pitch;
         p.H = H;
         p.W = W;
         p.FH = FH;
         p.FW = FW;
-        p.D = groups[g];
+        p.D = Dg;
         p.maps = maps;
         p.map_iter0 = maps_iter0 + passes;
         p.map_iter_stride = maps_iter_stride;
         p.map_plane = (long long)FH * FW;
-        if (last && !final_to_frame) {
+        p.err = ctx->err_word;
+        int nxt = -1;
+        if (last && !out_is_frame) {
             p.dst = out;
             p.dst_is_output = 1;
             p.dst_plane = (long long)H * W;
             p.dst_pitch = W;
         } else if (last) {
             p.dst = out;
-            p.dst_is_output = 0;
             p.dst_plane = (long long)FH * out_pitch;
             p.dst_pitch = out_pitch;
         } else {
-            p.dst = ctx->frames[g & 1];
-            p.dst_is_output = 0;
+            nxt = cur == 0 ? 1 : 0;
+            void *f = frame(nxt);
+            if (!f) return OSBF_ENOMEM;
+            p.dst = f;
             p.dst_plane = (long long)FH * FWp;
             p.dst_pitch = FWp;
         }
-        int ty0 = 0, ty1 = (FH - 1) / kTH, tx0 = 0, tx1 = (FW - 1) / kTW;
+        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1) / v2::TW;
         if (p.dst_is_output && !maps) {  // with maps, every frame pixel's selection is recorded
-            ty0 = r / kTH;
-            ty1 = (r + H - 1) / kTH;
-            tx0 = r / kTW;
-            tx1 = (r + W - 1) / kTW;
+            ty0 = r / v2::TH;
+            ty1 = (r + H - 1) / v2::TH;
+            tx0 = r / v2::TW;
+            tx1 = (r + W - 1) / v2::TW;
         }
         p.ty_off = ty0;
         p.tx_off = tx0;
-        const bool u8first = u8 && g == 0;
-        // planes go in grid.z; split if there are more than the grid allows
-        for (int p0 = 0; p0 < P; p0 += 65535) {
-            const int np = P - p0 < 65535 ? P - p0 : 65535;
-            FwdParams q = p;
-            const size_t ses = (u8first ? 1 : (src_is_input ? elem_size(dtype) : fes));
-            const size_t des = p.dst_is_output ? (dtype == OSBF_U8 ? 4 : elem_size(dtype)) : fes;
-            q.src = (const char *)p.src + ses * (size_t)p0 * p.src_plane;
-            q.dst = (char *)p.dst + des * (size_t)p0 * p.dst_plane;
-            if (q.maps) q.maps = p.maps + (size_t)p0 * p.map_plane;
-            dim3 grid(tx1 - tx0 + 1, ty1 - ty0 + 1, np);
-            cudaError_t e = launch_group(st, u8first, r, tie != 0, maps != nullptr, q, grid, s);
-            if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "forward launch failed: %s", cudaGetErrorString(e));
-            ctx->last_launches += 1;
+        p.tiles_x = tx1 - tx0 + 1;
+        p.tiles_y = ty1 - ty0 + 1;
+        const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
+        if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
+        p.ntiles = (int)ntiles;
+        // one pass written straight from registers into a destination frame
+        const bool direct = Dg == 1 && !p.dst_is_output && L.EX == r && tie == 0 && !maps;
+        int occ = occupancy_v2(st, r, tie != 0, maps != nullptr, direct, Dg);
+        if (occ < 1) occ = 1;
+        const long long g = (long long)occ * ctx->sms;
+        const int grid = (int)(g < ntiles ? g : ntiles);
+        cudaError_t e = launch_v2(st, r, tie != 0, maps != nullptr, direct, map, p, grid, s);
+        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "forward launch failed: %s", cudaGetErrorString(e));
+        ctx->last_launches += 1;
+        passes += Dg;
+        if (nxt >= 0) {
+            cur = nxt;
+            src = fb[nxt];
+            src_pitch = FWp;
         }
-        passes += groups[g];
-        src = p.dst;
-        src_is_input = 0;
-        src_plane = p.dst_plane;
-        src_pitch = p.dst_pitch;
     }
     return OSBF_OK;
 }
@@ -280,6 +368,12 @@ osbf_status osbf_create(osbf_ctx **out, int device) {
     ctx->sms = v;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     ctx->smem_optin = (size_t)v;
+    if (cudaMalloc(&ctx->err_word, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(ctx->err_word, 0, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return OSBF_ENOMEM;
+    }
     *out = ctx;
     return OSBF_OK;
 }
@@ -294,6 +388,7 @@ void osbf_destroy(osbf_ctx *ctx) {
         if (p) cudaFree(p);
     if (ctx->dev_in) cudaFree(ctx->dev_in);
     if (ctx->dev_out) cudaFree(ctx->dev_out);
+    if (ctx->err_word) cudaFree(ctx->err_word);
     osbf_batched_free(ctx);
     delete ctx;
 }
@@ -301,6 +396,19 @@ void osbf_destroy(osbf_ctx *ctx) {
 const char *osbf_last_error(const osbf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int osbf_last_launch_count(const osbf_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+osbf_status osbf_check(osbf_ctx *ctx) {
+    if (!ctx) return OSBF_EINVAL;
+    DeviceGuard g(ctx->device);
+    OSBF_CK(cudaDeviceSynchronize());
+    unsigned int w = 0;
+    OSBF_CK(cudaMemcpy(&w, ctx->err_word, sizeof w, cudaMemcpyDeviceToHost));
+    if (w) {
+        OSBF_CK(cudaMemset(ctx->err_word, 0, sizeof w));
+        return fail(ctx, OSBF_ETIMEOUT, "a bounded device-side wait gave up (error word 0x%x)", w);
+    }
+    return OSBF_OK;
+}
 
 osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
                            osbf_dtype dtype, const osbf_options *opts, void *stream) {
@@ -380,6 +488,12 @@ osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, in
     if (e) return e;
     OSBF_CK(cudaMemcpyAsync(out, ctx->dev_out, out_bytes, cudaMemcpyDeviceToHost, s));
     OSBF_CK(cudaStreamSynchronize(s));
+    unsigned int w = 0;
+    OSBF_CK(cudaMemcpy(&w, ctx->err_word, sizeof w, cudaMemcpyDeviceToHost));
+    if (w) {
+        cudaMemset(ctx->err_word, 0, sizeof w);
+        return fail(ctx, OSBF_ETIMEOUT, "a bounded device-side wait gave up");
+    }
     return OSBF_OK;
 }
 
@@ -462,6 +576,7 @@ osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *gr
 }  // extern "C"
 
 // accessors for the other translation units
+unsigned int *osbf_ctx_err_word(osbf_ctx *ctx) { return ctx->err_word; }
 void *osbf_ctx_workspace(osbf_ctx *ctx, int slot, size_t bytes, osbf_status *st) {
     *st = ensure(ctx, &ctx->ws[slot], &ctx->ws_bytes[slot], bytes);
     return *st == OSBF_OK ? ctx->ws[slot] : nullptr;

@@ -1,0 +1,523 @@
+// osbf_fwd2.cuh -- persistent, TMA-fed forward kernel of the One-Sided Box Filter (sm_103a).
+//
+// Same arithmetic as osbf_fwd.cuh (Eq. (6)-(13), the box kernels, Algorithm 2, the
+// appendix's zero-outside-the-frame rule), organised for throughput:
+//   * persistent CTAs walk the tile list; each tile's region (tile + halo) of the
+//     source frame arrives by one TMA tensor load (out-of-frame elements are filled
+//     with zeros by the copy engine, which is exactly the appendix's boundary), and
+//     the next tile's load is issued as soon as the current input buffer is dead;
+//   * pass V (one thread per column pair) keeps running column sums a(y) and writes
+//     the pair (a(y), a(y + r)) -- the up and down column sums of one output row --
+//     interleaved, so pass H reads both with one 16-byte load;
+//   * pass H (one thread per row segment) keeps the left row sums of (a, b) as a
+//     float2 and runs the window sums and scores with packed f32x2 instructions
+//     (two windows per instruction); only the eight-way selection is scalar;
+//   * tiles whose region lies inside the frame skip the per-pixel frame mask.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "osbf_fwd.cuh"
+
+namespace osbf {
+namespace v2 {
+
+constexpr int TH = 32;   // tile rows
+constexpr int TW = 128;  // tile columns
+constexpr int SW = 32;   // pass-H segment width
+constexpr int NT = 128;  // threads per CTA
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a tile load that has not landed in 1 s is an error
+
+struct Layout2 {
+    int EY, EX, RH0, RW0;
+    int BX;      // TMA box width (elements) = row pitch of the input buffer
+    int PU;      // float row pitch of U buffers (PU % 8 == 4: conflict-free row-owner float4 access)
+    int P2;      // float2 row pitch of the (a, b) buffer (P2 % 4 == 2)
+    int in_bytes;  // bytes of one TMA box
+    int off_in, off_uf, off_ab, off_ua, off_ub, bytes;  // byte offsets (128-aligned)
+};
+
+__host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
+
+// direct: a single pass whose results go straight from registers to the destination
+// frame (no U^1 buffer in shared memory)
+template <typename T>
+__host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false) {
+    Layout2 L;
+    const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
+    L.EY = D * R;
+    L.EX = round_up(D * R, xa);
+    L.RH0 = TH + 2 * L.EY;
+    L.RW0 = TW + 2 * L.EX;
+    // pass H sweeps full SW-wide segments over the widest output region (RW0 - 2R): the
+    // last segment reads up to SW + 2R + 3 columns past its start
+    const int xs_last = ((L.RW0 - 2 * R + SW - 1) / SW - 1) * SW;
+    L.PU = xs_last + SW + 2 * R + 4;
+    if (L.PU < L.RW0 + 8) L.PU = L.RW0 + 8;
+    while (L.PU % 8 != 4) ++L.PU;
+    L.P2 = L.PU + 2;
+    L.BX = sizeof(T) == 4 ? L.PU : round_up(L.PU, 8);
+    L.in_bytes = L.BX * L.RH0 * (int)sizeof(T);
+    const int rh1 = L.RH0 - 2 * R;  // rows of U^1 and of the (a, b) buffer
+    int off = 0;
+    L.off_in = off;
+    off = align128(off + L.in_bytes);
+    L.off_uf = off;  // float copy of the input (16-bit storage only)
+    if (sizeof(T) != 4) off = align128(off + L.RH0 * L.PU * 4);
+    L.off_ab = off;
+    off = align128(off + rh1 * L.P2 * 8);
+    L.off_ua = off;
+    if (!direct) off = align128(off + rh1 * L.PU * 4);
+    L.off_ub = off;
+    if (D >= 2) off = align128(off + rh1 * L.PU * 4);
+    L.bytes = off + 16;  // + mbarrier
+    return L;
+}
+
+struct Fwd2Params {
+    void *dst;                 // frame (dst_is_output = 0) or the caller's output
+    int dst_is_output;
+    long long dst_plane;
+    int dst_pitch;
+    uint8_t *maps;
+    int map_iter0;
+    long long map_iter_stride, map_plane;
+    int H, W, FH, FW;
+    int D;
+    int tiles_x, tiles_y, ntiles;  // tile grid; ntiles = tiles_x * tiles_y * planes
+    int ty_off, tx_off;
+    unsigned int *err;         // device error word (bit 0: a bounded wait gave up)
+};
+
+// ----------------------------------------------------------------------------------
+// TMA / mbarrier primitives (inline PTX)
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar,
+                                            uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for an mbarrier phase, giving up after kWaitNs (returns false then).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// packed f32x2 helpers
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// storage-type stores of four floats
+template <typename T> __device__ __forceinline__ void cvt_store4(T *p, float4 v);
+template <> __device__ __forceinline__ void cvt_store4<float>(float *p, float4 v) {
+    *reinterpret_cast<float4 *>(p) = v;
+}
+template <> __device__ __forceinline__ void cvt_store4<__half>(__half *p, float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 w;
+    w.x = *reinterpret_cast<uint32_t *>(&a);
+    w.y = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(p) = w;
+}
+template <> __device__ __forceinline__ void cvt_store4<__nv_bfloat16>(__nv_bfloat16 *p, float4 v) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 w;
+    w.x = *reinterpret_cast<uint32_t *>(&a);
+    w.y = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(p) = w;
+}
+
+// ----------------------------------------------------------------------------------
+// pass V on column pairs: a(y) = sum_{y-R..y} U(., x); writes AB[y-2R][x] = (a(y-R), a(y))
+// for region rows y in [2R, RH): the up and down column sums of output row y - 2R + R.
+// ----------------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float2 *__restrict__ AB, int p2, int RH,
+                                        int RW) {
+    constexpr int P = R + 1;
+    const int npairs = (RW + 1) >> 1;
+    for (int item = threadIdx.x; item < npairs; item += NT) {
+        const int c = item * 2;
+        const float *col = U + c;
+        float4 *abcol = reinterpret_cast<float4 *>(AB + c);  // (a_c, b_c, a_c+1, b_c+1)
+        float2 ring[P];
+        float2 hist[P];  // a(s) by slot, kept R steps for the pair (a(s-R), a(s))
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            ring[k] = make_float2(0.f, 0.f);
+            hist[k] = make_float2(0.f, 0.f);
+        }
+        float2 acc = make_float2(0.f, 0.f);
+        for (int s0 = 0; s0 < RH; s0 += P) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int s = s0 + k;
+                if (s < RH) {
+                    const float2 v = *reinterpret_cast<const float2 *>(col + s * pu);
+                    if (k == P - 1) {  // the ring holds the whole window: re-form the sum
+                        ring[k] = v;
+                        acc = ring[0];
+#pragma unroll
+                        for (int i = 1; i < P; ++i) acc = add2(acc, ring[i]);
+                    } else {
+                        acc = add2(acc, sub2(v, ring[k]));
+                        ring[k] = v;
+                    }
+                    hist[k] = acc;
+                    if (s >= 2 * R) {
+                        const float2 up = hist[(k + 1) % P];  // a(s - R): slot (s - R) mod (R + 1)
+                        abcol[(s - 2 * R) * (p2 >> 1)] = make_float4(up.x, acc.x, up.y, acc.y);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// pass H: lane = row, warp = 32 rows x one SW-column segment
+// ----------------------------------------------------------------------------------
+struct Geom2 {
+    int RHo, RWo;
+    int fy0, fx0, FH, FW;
+    int iy0, iy1, ix0, ix1;
+};
+
+template <int R, bool TIE_APP, bool IDX>
+__device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, float2 d87, float u, float &out, int &m) {
+    // d_i for N1..N8
+    const float dv[9] = {0.f, d41.y, d32.y, d32.x, d41.x, d56.x, d56.y, d87.y, d87.x};
+    float d[8];
+    int id[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        id[k] = tie_window<TIE_APP>(k);
+        d[k] = dv[id[k]];
+    }
+    pick<IDX>(d[0], id[0], d[1], id[1]);
+    pick<IDX>(d[2], id[2], d[3], id[3]);
+    pick<IDX>(d[4], id[4], d[5], id[5]);
+    pick<IDX>(d[6], id[6], d[7], id[7]);
+    pick<IDX>(d[0], id[0], d[2], id[2]);
+    pick<IDX>(d[4], id[4], d[6], id[6]);
+    pick<IDX>(d[0], id[0], d[4], id[4]);
+    out = u + d[0];
+    m = id[0];
+}
+
+// Output of pass H: a float buffer in shared memory (the next fused pass reads it), or
+// -- DIRECT -- four results at a time straight into the destination frame in global
+// memory (storage type T, 16- or 8-byte stores, rows and columns outside the frame skipped).
+template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT>
+__device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, const float2 *__restrict__ AB, int p2,
+                                        float *__restrict__ Uout, int pu_out, T *__restrict__ gdst,
+                                        long long gpitch, const Geom2 &g, uint8_t *__restrict__ mplane) {
+    constexpr int P = (R + 1 + 3) & ~3;  // ring period: >= R+1, a multiple of 4
+    constexpr int NS = SW + 2 * R;       // sweep steps of one segment (2R of warm-up)
+    constexpr float iq = 1.0f / float((R + 1) * (R + 1));
+    constexpr float ih = 1.0f / float((R + 1) * (2 * R + 1));
+    const float2 iq2 = make_float2(iq, iq), ih2 = make_float2(ih, ih);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nrb = (g.RHo + 31) >> 5;
+    const int nseg = (g.RWo + SW - 1) / SW;
+    for (int item = warp; item < nrb * nseg; item += NT / 32) {
+        const int rbk = item % nrb, seg = item / nrb;
+        const int yo = rbk * 32 + lane;
+        const bool row_ok = yo < g.RHo;
+        const int yr = row_ok ? yo : g.RHo - 1;
+        const int xs = seg * SW;
+        const float4 *abrow = reinterpret_cast<const float4 *>(AB + yr * p2 + xs);
+        const float4 *urow = reinterpret_cast<const float4 *>(Uin + (yr + R) * pu_in + xs);
+        float4 *orow = reinterpret_cast<float4 *>(Uout + yr * pu_out + xs);
+        const int fy = g.fy0 + yo;
+        const bool row_store = DIRECT ? (row_ok && (unsigned)fy < (unsigned)g.FH) : row_ok;
+        T *grow = DIRECT ? gdst + (long long)(row_store ? fy : 0) * gpitch + g.fx0 + xs : nullptr;
+        const bool row_map = MAPS && row_ok && (unsigned)fy < (unsigned)g.FH && yo >= g.iy0 && yo < g.iy1;
+        float2 rab[P], hab[P];
+        float ru[P], hu[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            rab[k] = make_float2(0.f, 0.f);
+            ru[k] = 0.f;
+        }
+        float2 ABL = make_float2(0.f, 0.f);  // (AL, BL): left row sums of a and b
+        float UL = 0.f;
+        float4 vab = make_float4(0.f, 0.f, 0.f, 0.f), vu = vab;
+        float o[4];
+        // the whole segment is unrolled: ring slots, loads, warm-up and stores are static
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            const int k = t % P;
+            if ((t & 1) == 0) vab = abrow[t >> 1];
+            if ((t & 3) == 0) vu = urow[t >> 2];
+            const float2 ab = (t & 1) ? make_float2(vab.z, vab.w) : make_float2(vab.x, vab.y);
+            const float u = f4get(vu, t & 3);
+            if (R <= 3 || k == P - 1) {
+                // direct sum over the ring's last R+1 entries (cheap for small r; resets
+                // the running sums' FP32 drift once per ring period for large r)
+                rab[k] = ab;
+                ru[k] = u;
+                ABL = ab;
+                UL = u;
+#pragma unroll
+                for (int i = 1; i <= R; ++i) {
+                    ABL = add2(ABL, rab[(k + P - i) % P]);
+                    UL += ru[(k + P - i) % P];
+                }
+            } else {
+                const int so = (k + 2 * P - R - 1) % P;  // the value leaving the window
+                ABL = add2(ABL, sub2(ab, rab[so]));
+                UL += u - ru[so];
+                rab[k] = ab;
+                ru[k] = u;
+            }
+            hab[k] = ABL;
+            hu[k] = UL;
+            if (t >= 2 * R) {
+                const int sl = (k + P - R) % P;  // column x = t - R; (AL, BL) at x+R is current
+                const float2 ABx = hab[sl];      // (AL(x), BL(x)) = (N4, N1)
+                const float2 abx = rab[sl];      // (a(x), b(x))
+                const float ULx = hu[sl];
+                const float ux = ru[sl];
+                const float2 nu = make_float2(-ux, -ux);
+                const float2 s87 = sub2(add2(ABx, ABL), abx);                          // (N8, N7)
+                const float2 s56 = make_float2(ABx.x + ABx.y - ULx, ABL.x + ABL.y - UL);  // (N5, N6)
+                const float2 d41 = fma2(ABx, iq2, nu);
+                const float2 d32 = fma2(ABL, iq2, nu);  // (N3, N2) = (AL(x+r), BL(x+r))
+                const float2 d56 = fma2(s56, ih2, nu);
+                const float2 d87 = fma2(s87, ih2, nu);
+                float outv;
+                int m;
+                select2<R, TIE_APP, MAPS>(d41, d32, d56, d87, ux, outv, m);
+                const int xo = xs + t - 2 * R;
+                o[(t - 2 * R) & 3] = storage_round<T>(outv);
+                if (MAPS) {
+                    const int fx = g.fx0 + xo;
+                    if (row_map && (unsigned)fx < (unsigned)g.FW && xo >= g.ix0 && xo < g.ix1)
+                        mplane[(long long)fy * g.FW + fx] = (uint8_t)m;
+                }
+                if (((t - 2 * R) & 3) == 3) {
+                    const float4 v = make_float4(o[0], o[1], o[2], o[3]);
+                    if (DIRECT) {
+                        if (row_store && g.fx0 + xo - 3 < g.FW) cvt_store4<T>(grow + (t - 2 * R - 3), v);
+                    } else if (row_ok) {
+                        orow[(t - 2 * R) >> 2] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Zero the cells of a fused intermediate region that lie outside the padded frame (the
+// next pass must read zeros there, as the appendix's convolution does).
+__device__ __forceinline__ void zero_outside(float *__restrict__ U, int pu, int RHo, int RWo, int fy0, int fx0, int FH,
+                                             int FW) {
+    for (int i = threadIdx.x; i < RHo * RWo; i += NT) {
+        const int y = i / RWo, x = i % RWo;
+        if ((unsigned)(fy0 + y) >= (unsigned)FH || (unsigned)(fx0 + x) >= (unsigned)FW) U[y * pu + x] = 0.f;
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// the persistent kernel
+// ----------------------------------------------------------------------------------
+// DIRECT: one pass per launch whose results go from registers straight into the
+// destination frame (needs D == 1, EX == R and a frame destination); otherwise every
+// pass lands in shared memory and the tile interior is copied out at the end.
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
+__global__ void __launch_bounds__(NT, 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
+    extern __shared__ __align__(128) unsigned char smem2[];
+    const Layout2 L = make_layout2<T>(R, p.D, DIRECT);
+    T *bin = reinterpret_cast<T *>(smem2 + L.off_in);
+    float *uf = reinterpret_cast<float *>(smem2 + (sizeof(T) == 4 ? L.off_in : L.off_uf));
+    float2 *AB = reinterpret_cast<float2 *>(smem2 + L.off_ab);
+    float *Ua = reinterpret_cast<float *>(smem2 + L.off_ua);
+    float *Ub = reinterpret_cast<float *>(smem2 + L.off_ub);
+    const uint32_t bar = smem_u32(smem2 + L.bytes - 16);
+    const int pu0 = sizeof(T) == 4 ? L.BX : L.PU;  // pitch of U^0 as a float buffer
+
+    const int tiles_per_plane = p.tiles_x * p.tiles_y;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile) {
+        const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
+        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
+        tma_load_3d(smem_u32(bin), &src, tx0 - L.EX, ty0 - L.EY, plane, bar, (uint32_t)L.in_bytes);
+    };
+    auto prefetch = [&](int tile) {
+        const int next = tile + gridDim.x;
+        if (next < p.ntiles && threadIdx.x == 0) {
+            fence_proxy_async();
+            issue(next);
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (tile < p.ntiles && threadIdx.x == 0) issue(tile);
+    uint32_t phase = 0;
+    for (; tile < p.ntiles; tile += gridDim.x) {
+        const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
+        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
+        // wait for this tile's region (bounded: a copy that never lands is reported, not waited on forever)
+        const bool timed_out = !mbar_wait_bounded(bar, phase);
+        if (__syncthreads_or(timed_out)) {
+            if (threadIdx.x == 0) atomicOr(p.err, 1u);
+            return;
+        }
+        phase ^= 1;
+
+        bool prefetched = false;
+        if (sizeof(T) != 4) {  // widen the 16-bit box into the float buffer, then the box is free
+            const int w4 = (L.PU - 4) / 4;
+            for (int i = threadIdx.x; i < L.RH0 * w4; i += NT) {
+                const int y = i / w4, x = (i % w4) * 4;
+                const T *q = bin + y * L.BX + x;
+                *reinterpret_cast<float4 *>(uf + y * L.PU + x) =
+                    make_float4(to_f(q[0]), to_f(q[1]), to_f(q[2]), to_f(q[3]));
+            }
+            __syncthreads();
+            prefetch(tile);
+            prefetched = true;
+        }
+        const bool interior = ty0 - L.EY >= 0 && tx0 - L.EX >= 0 && ty0 + TH + L.EY <= p.FH &&
+                              tx0 + TW + L.EX <= p.FW;
+        T *gdst = reinterpret_cast<T *>(p.dst) + (long long)plane * p.dst_plane;
+        for (int j = 1; j <= p.D; ++j) {
+            const float *Uin = j == 1 ? uf : ((j & 1) ? Ub : Ua);
+            const int puin = j == 1 ? pu0 : L.PU;
+            float *Uout = (j & 1) ? Ua : Ub;
+            const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
+            pass_v2<R>(Uin, puin, AB, L.P2, RH, RW);
+            __syncthreads();
+            Geom2 g;
+            g.RHo = RH - 2 * R;
+            g.RWo = RW - 2 * R;
+            g.fy0 = ty0 - (L.EY - j * R);
+            g.fx0 = tx0 - (L.EX - j * R);
+            g.FH = p.FH;
+            g.FW = p.FW;
+            g.iy0 = L.EY - j * R;
+            g.iy1 = g.iy0 + TH;
+            g.ix0 = L.EX - j * R;
+            g.ix1 = g.ix0 + TW;
+            uint8_t *mplane = nullptr;
+            if (MAPS && p.maps)
+                mplane =
+                    p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, AB, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            __syncthreads();
+            if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
+                prefetch(tile);
+                prefetched = true;
+            }
+            if (!DIRECT && j < p.D && !interior) {
+                zero_outside(Uout, L.PU, g.RHo, g.RWo, g.fy0, g.fx0, p.FH, p.FW);
+                __syncthreads();
+            }
+        }
+        if (DIRECT) continue;  // results already in the destination frame
+
+        // store the tile interior of U^D (row-wise, coalesced)
+        const float *UD = (p.D & 1) ? Ua : Ub;
+        const int cx = L.EX - p.D * R;
+        if (!p.dst_is_output) {
+            if ((cx & 3) == 0) {
+                for (int i = threadIdx.x; i < TH * (TW / 4); i += NT) {
+                    const int y = i / (TW / 4), x = (i % (TW / 4)) * 4;
+                    const int fy = ty0 + y, fx = tx0 + x;
+                    if (fy < p.FH && fx < p.FW)
+                        cvt_store4<T>(gdst + (long long)fy * p.dst_pitch + fx,
+                                      *reinterpret_cast<const float4 *>(UD + y * L.PU + cx + x));
+                }
+            } else {
+                for (int i = threadIdx.x; i < TH * TW; i += NT) {
+                    const int y = i / TW, x = i % TW;
+                    const int fy = ty0 + y, fx = tx0 + x;
+                    if (fy < p.FH && fx < p.FW) gdst[(long long)fy * p.dst_pitch + fx] = from_f<T>(UD[y * L.PU + cx + x]);
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < TH * TW; i += NT) {
+                const int y = i / TW, x = i % TW;
+                const int oy = ty0 + y - R, ox = tx0 + x - R;
+                if (oy >= 0 && oy < p.H && ox >= 0 && ox < p.W)
+                    gdst[(long long)oy * p.dst_pitch + ox] = from_f<T>(UD[y * L.PU + cx + x]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
+cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream) {
+    const Layout2 L = make_layout2<T>(R, p.D, DIRECT);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, L.bytes, stream>>>(src, p);
+    return cudaGetLastError();
+}
+
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
+int occupancy_fwd2(int D) {
+    const Layout2 L = make_layout2<T>(R, D, DIRECT);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, L.bytes) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace v2
+}  // namespace osbf

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "osbf_fwd.cuh"
+#include "osbf_fwd2.cuh"
 
 // every radius with a compiled kernel
 #define OSBF_FOR_EACH_R(X) \
@@ -14,15 +15,30 @@ namespace osbf {
 
 enum class Storage { F32 = 0, F16 = 1, BF16 = 2, U8 = 3 };
 
-// One fused group of forward passes (D = p.D) on the tile grid `grid`.
-cudaError_t launch_fwd_f32_paper(int R, bool maps, const FwdParams &p, dim3 grid, cudaStream_t s);
-cudaError_t launch_fwd_f32_appendix(int R, bool maps, const FwdParams &p, dim3 grid, cudaStream_t s);
-cudaError_t launch_fwd_f16(int R, bool tie_app, bool maps, const FwdParams &p, dim3 grid, cudaStream_t s);
-cudaError_t launch_fwd_bf16(int R, bool tie_app, bool maps, const FwdParams &p, dim3 grid, cudaStream_t s);
+// The exact first pass on 8-bit input (the first-pass tile kernel of osbf_fwd.cuh).
 cudaError_t launch_fwd_u8(int R, bool tie_app, const FwdParams &p, dim3 grid, cudaStream_t s);
 
-// dynamic shared memory of one forward CTA
+// dynamic shared memory of one forward CTA (first-pass kernel)
 size_t fwd_smem(Storage st, int R, int D);
+
+// persistent TMA-fed forward (frames in, frame or cropped output out)
+cudaError_t launch_fwd2_f32(int R, bool tie_app, bool maps, bool direct, const CUtensorMap &src, const v2::Fwd2Params &p, int grid,
+                            cudaStream_t s);
+cudaError_t launch_fwd2_f16(int R, bool tie_app, bool maps, bool direct, const CUtensorMap &src, const v2::Fwd2Params &p, int grid,
+                            cudaStream_t s);
+cudaError_t launch_fwd2_bf16(int R, bool tie_app, bool maps, bool direct, const CUtensorMap &src, const v2::Fwd2Params &p, int grid,
+                             cudaStream_t s);
+int occupancy_fwd2_f32(int R, bool tie_app, bool maps, bool direct, int D);
+int occupancy_fwd2_f16(int R, bool tie_app, bool maps, bool direct, int D);
+int occupancy_fwd2_bf16(int R, bool tie_app, bool maps, bool direct, int D);
+size_t smem_fwd2_f32(int R, int D, bool direct);
+size_t smem_fwd2_f16(int R, int D, bool direct);
+size_t smem_fwd2_bf16(int R, int D, bool direct);
+
+bool encode_frame_map(CUtensorMap *map, Storage st, const void *base, int FW, int FH, int P, int pitch, int box_w,
+                      int box_h);
+cudaError_t launch_pad_replicate(Storage st, const void *in, void *frame, int P, int H, int W, int R, int FH, int FW,
+                                 int FWp, cudaStream_t s);
 
 // elementwise helpers (osbf_misc.cu)
 cudaError_t launch_u8_to_f32(const uint8_t *in, float *out, long long n, cudaStream_t s);

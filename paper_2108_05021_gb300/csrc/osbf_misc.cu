@@ -39,3 +39,40 @@ size_t fwd_smem(Storage st, int R, int D) {
 }
 
 }  // namespace osbf
+
+// ------------------------------------------------------------------------------------
+// the appendix's replicate padding: frame(fy, fx) = in(clamp(fy - R), clamp(fx - R))
+// ------------------------------------------------------------------------------------
+namespace osbf {
+
+template <typename T>
+__global__ void pad_replicate_kernel(const T *__restrict__ in, T *__restrict__ frame, int H, int W, int R, int FW,
+                                     int FWp) {
+    const int fy = blockIdx.y, plane = blockIdx.z;
+    const int y = min(max(fy - R, 0), H - 1);
+    const T *src = in + ((long long)plane * H + y) * W;
+    T *dst = frame + ((long long)plane * gridDim.y + fy) * FWp;
+    for (int fx = blockIdx.x * blockDim.x + threadIdx.x; fx < FW; fx += gridDim.x * blockDim.x)
+        dst[fx] = src[min(max(fx - R, 0), W - 1)];
+}
+
+cudaError_t launch_pad_replicate(Storage st, const void *in, void *frame, int P, int H, int W, int R, int FH, int FW,
+                                 int FWp, cudaStream_t s) {
+    dim3 grid((FW + 255) / 256 < 8 ? (FW + 255) / 256 : 8, FH, P);
+    switch (st) {
+    case Storage::F32:
+        pad_replicate_kernel<float><<<grid, 256, 0, s>>>((const float *)in, (float *)frame, H, W, R, FW, FWp);
+        break;
+    case Storage::F16:
+        pad_replicate_kernel<__half><<<grid, 256, 0, s>>>((const __half *)in, (__half *)frame, H, W, R, FW, FWp);
+        break;
+    case Storage::BF16:
+        pad_replicate_kernel<__nv_bfloat16>
+            <<<grid, 256, 0, s>>>((const __nv_bfloat16 *)in, (__nv_bfloat16 *)frame, H, W, R, FW, FWp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace osbf
