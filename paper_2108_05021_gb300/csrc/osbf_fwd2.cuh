@@ -6,13 +6,13 @@
 //     source frame arrives by one TMA tensor load (out-of-frame elements are filled
 //     with zeros by the copy engine, which is exactly the appendix's boundary), and
 //     the next tile's load is issued as soon as the current input buffer is dead;
-//   * pass V (one thread per column pair) keeps running column sums a(y) and writes
-//     the pair (a(y), a(y + r)) -- the up and down column sums of one output row --
-//     interleaved, so pass H reads both with one 16-byte load;
-//   * pass H (one thread per row segment) keeps the left row sums of (a, b) as a
-//     float2 and runs the window sums and scores with packed f32x2 instructions
-//     (two windows per instruction); only the eight-way selection is scalar;
-//   * tiles whose region lies inside the frame skip the per-pixel frame mask.
+//   * pass V (one thread per column pair) keeps running column sums a(y) with packed
+//     f32x2 instructions; pass H reads a(y) (up sum) and a(y + r) (down sum) of its row;
+//   * pass H (one thread per row segment) keeps the left row sums (AL, BL) as a float2
+//     and runs the window sums and scores with packed f32x2 instructions (two windows
+//     per instruction); only the eight-way selection is scalar;
+//   * single-pass launches write results from registers straight into the
+//     destination frame, and the whole sweep of a segment is unrolled.
 #pragma once
 
 #include <cuda.h>
@@ -36,7 +36,7 @@ struct Layout2 {
     int EY, EX, RH0, RW0;
     int BX;      // TMA box width (elements) = row pitch of the input buffer
     int PU;      // float row pitch of U buffers (PU % 8 == 4: conflict-free row-owner float4 access)
-    int P2;      // float2 row pitch of the (a, b) buffer (P2 % 4 == 2)
+    int P2;      // float row pitch of the column-sum field A
     int in_bytes;  // bytes of one TMA box
     int off_in, off_uf, off_ab, off_ua, off_ub, bytes;  // byte offsets (128-aligned)
 };
@@ -59,7 +59,7 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     L.PU = xs_last + SW + 2 * R + 4;
     if (L.PU < L.RW0 + 8) L.PU = L.RW0 + 8;
     while (L.PU % 8 != 4) ++L.PU;
-    L.P2 = L.PU + 2;
+    L.P2 = L.PU;  // float row pitch of the column-sum field A (same conflict-free pitch)
     L.BX = sizeof(T) == 4 ? L.PU : round_up(L.PU, 8);
     L.in_bytes = L.BX * L.RH0 * (int)sizeof(T);
     const int rh1 = L.RH0 - 2 * R;  // rows of U^1 and of the (a, b) buffer
@@ -69,7 +69,7 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     L.off_uf = off;  // float copy of the input (16-bit storage only)
     if (sizeof(T) != 4) off = align128(off + L.RH0 * L.PU * 4);
     L.off_ab = off;
-    off = align128(off + rh1 * L.P2 * 8);
+    off = align128(off + (L.RH0 - R) * L.P2 * 4);
     L.off_ua = off;
     if (!direct) off = align128(off + rh1 * L.PU * 4);
     L.off_ub = off;
@@ -173,47 +173,45 @@ template <> __device__ __forceinline__ void cvt_store4<__nv_bfloat16>(__nv_bfloa
 }
 
 // ----------------------------------------------------------------------------------
-// pass V on column pairs: a(y) = sum_{y-R..y} U(., x); writes AB[y-2R][x] = (a(y-R), a(y))
-// for region rows y in [2R, RH): the up and down column sums of output row y - 2R + R.
+// pass V on column pairs: a(y) = sum_{y-R..y} U(., x), stored at A[y - R] for region rows
+// y in [R, RH).  NRH > 0: the row count is a compile-time constant (single-pass
+// launches), so the sweep is fully unrolled.
 // ----------------------------------------------------------------------------------
-template <int R>
-__device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float2 *__restrict__ AB, int p2, int RH,
+template <int R, int NRH>
+__device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float *__restrict__ A, int pa, int RH_rt,
                                         int RW) {
     constexpr int P = R + 1;
+    const int RH = NRH > 0 ? NRH : RH_rt;
     const int npairs = (RW + 1) >> 1;
     for (int item = threadIdx.x; item < npairs; item += NT) {
         const int c = item * 2;
         const float *col = U + c;
-        float4 *abcol = reinterpret_cast<float4 *>(AB + c);  // (a_c, b_c, a_c+1, b_c+1)
+        float2 *acol = reinterpret_cast<float2 *>(A + c);
         float2 ring[P];
-        float2 hist[P];  // a(s) by slot, kept R steps for the pair (a(s-R), a(s))
 #pragma unroll
-        for (int k = 0; k < P; ++k) {
-            ring[k] = make_float2(0.f, 0.f);
-            hist[k] = make_float2(0.f, 0.f);
-        }
+        for (int k = 0; k < P; ++k) ring[k] = make_float2(0.f, 0.f);
         float2 acc = make_float2(0.f, 0.f);
-        for (int s0 = 0; s0 < RH; s0 += P) {
+        auto step = [&](int s, int k) {
+            const float2 v = *reinterpret_cast<const float2 *>(col + s * pu);
+            if (k == P - 1) {  // the ring holds the whole window: re-form the sum
+                ring[k] = v;
+                acc = ring[0];
 #pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const int s = s0 + k;
-                if (s < RH) {
-                    const float2 v = *reinterpret_cast<const float2 *>(col + s * pu);
-                    if (k == P - 1) {  // the ring holds the whole window: re-form the sum
-                        ring[k] = v;
-                        acc = ring[0];
+                for (int i = 1; i < P; ++i) acc = add2(acc, ring[i]);
+            } else {
+                acc = add2(acc, sub2(v, ring[k]));
+                ring[k] = v;
+            }
+            if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
+        };
+        if (NRH > 0) {
 #pragma unroll
-                        for (int i = 1; i < P; ++i) acc = add2(acc, ring[i]);
-                    } else {
-                        acc = add2(acc, sub2(v, ring[k]));
-                        ring[k] = v;
-                    }
-                    hist[k] = acc;
-                    if (s >= 2 * R) {
-                        const float2 up = hist[(k + 1) % P];  // a(s - R): slot (s - R) mod (R + 1)
-                        abcol[(s - 2 * R) * (p2 >> 1)] = make_float4(up.x, acc.x, up.y, acc.y);
-                    }
-                }
+            for (int s = 0; s < (NRH > 0 ? NRH : 1); ++s) step(s, s % P);
+        } else {
+            for (int s0 = 0; s0 < RH; s0 += P) {
+#pragma unroll
+                for (int k = 0; k < P; ++k)
+                    if (s0 + k < RH) step(s0 + k, k);
             }
         }
     }
@@ -254,7 +252,7 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
 // -- DIRECT -- four results at a time straight into the destination frame in global
 // memory (storage type T, 16- or 8-byte stores, rows and columns outside the frame skipped).
 template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT>
-__device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, const float2 *__restrict__ AB, int p2,
+__device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, const float *__restrict__ A, int pa,
                                         float *__restrict__ Uout, int pu_out, T *__restrict__ gdst,
                                         long long gpitch, const Geom2 &g, uint8_t *__restrict__ mplane) {
     constexpr int P = (R + 1 + 3) & ~3;  // ring period: >= R+1, a multiple of 4
@@ -271,49 +269,57 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const bool row_ok = yo < g.RHo;
         const int yr = row_ok ? yo : g.RHo - 1;
         const int xs = seg * SW;
-        const float4 *abrow = reinterpret_cast<const float4 *>(AB + yr * p2 + xs);
+        const float4 *arow = reinterpret_cast<const float4 *>(A + yr * pa + xs);        // a: up column sums
+        const float4 *brow = reinterpret_cast<const float4 *>(A + (yr + R) * pa + xs);  // b: down column sums
         const float4 *urow = reinterpret_cast<const float4 *>(Uin + (yr + R) * pu_in + xs);
         float4 *orow = reinterpret_cast<float4 *>(Uout + yr * pu_out + xs);
         const int fy = g.fy0 + yo;
         const bool row_store = DIRECT ? (row_ok && (unsigned)fy < (unsigned)g.FH) : row_ok;
         T *grow = DIRECT ? gdst + (long long)(row_store ? fy : 0) * gpitch + g.fx0 + xs : nullptr;
         const bool row_map = MAPS && row_ok && (unsigned)fy < (unsigned)g.FH && yo >= g.iy0 && yo < g.iy1;
-        float2 rab[P], hab[P];
-        float ru[P], hu[P];
+        float ra[P], rb[P], ru[P], hu[P];
+        float2 hab[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            rab[k] = make_float2(0.f, 0.f);
+            ra[k] = 0.f;
+            rb[k] = 0.f;
             ru[k] = 0.f;
         }
         float2 ABL = make_float2(0.f, 0.f);  // (AL, BL): left row sums of a and b
         float UL = 0.f;
-        float4 vab = make_float4(0.f, 0.f, 0.f, 0.f), vu = vab;
+        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va, vu = va;
         float o[4];
         // the whole segment is unrolled: ring slots, loads, warm-up and stores are static
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             const int k = t % P;
-            if ((t & 1) == 0) vab = abrow[t >> 1];
-            if ((t & 3) == 0) vu = urow[t >> 2];
-            const float2 ab = (t & 1) ? make_float2(vab.z, vab.w) : make_float2(vab.x, vab.y);
-            const float u = f4get(vu, t & 3);
+            if ((t & 3) == 0) {
+                va = arow[t >> 2];
+                vb = brow[t >> 2];
+                vu = urow[t >> 2];
+            }
+            const float a = f4get(va, t & 3), b = f4get(vb, t & 3), u = f4get(vu, t & 3);
             if (R <= 3 || k == P - 1) {
                 // direct sum over the ring's last R+1 entries (cheap for small r; resets
                 // the running sums' FP32 drift once per ring period for large r)
-                rab[k] = ab;
+                ra[k] = a;
+                rb[k] = b;
                 ru[k] = u;
-                ABL = ab;
-                UL = u;
+                float al = a, bl = b, ul = u;
 #pragma unroll
                 for (int i = 1; i <= R; ++i) {
-                    ABL = add2(ABL, rab[(k + P - i) % P]);
-                    UL += ru[(k + P - i) % P];
+                    al += ra[(k + P - i) % P];
+                    bl += rb[(k + P - i) % P];
+                    ul += ru[(k + P - i) % P];
                 }
+                ABL = make_float2(al, bl);
+                UL = ul;
             } else {
                 const int so = (k + 2 * P - R - 1) % P;  // the value leaving the window
-                ABL = add2(ABL, sub2(ab, rab[so]));
+                ABL = make_float2(ABL.x + (a - ra[so]), ABL.y + (b - rb[so]));
                 UL += u - ru[so];
-                rab[k] = ab;
+                ra[k] = a;
+                rb[k] = b;
                 ru[k] = u;
             }
             hab[k] = ABL;
@@ -321,11 +327,11 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
             if (t >= 2 * R) {
                 const int sl = (k + P - R) % P;  // column x = t - R; (AL, BL) at x+R is current
                 const float2 ABx = hab[sl];      // (AL(x), BL(x)) = (N4, N1)
-                const float2 abx = rab[sl];      // (a(x), b(x))
                 const float ULx = hu[sl];
                 const float ux = ru[sl];
                 const float2 nu = make_float2(-ux, -ux);
-                const float2 s87 = sub2(add2(ABx, ABL), abx);                          // (N8, N7)
+                const float2 sum = add2(ABx, ABL);
+                const float2 s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);          // (N8, N7)
                 const float2 s56 = make_float2(ABx.x + ABx.y - ULx, ABL.x + ABL.y - UL);  // (N5, N6)
                 const float2 d41 = fma2(ABx, iq2, nu);
                 const float2 d32 = fma2(ABL, iq2, nu);  // (N3, N2) = (AL(x+r), BL(x+r))
@@ -371,12 +377,12 @@ __device__ __forceinline__ void zero_outside(float *__restrict__ U, int pu, int 
 // destination frame (needs D == 1, EX == R and a frame destination); otherwise every
 // pass lands in shared memory and the tile interior is copied out at the end.
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
-__global__ void __launch_bounds__(NT, 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 8 ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
     extern __shared__ __align__(128) unsigned char smem2[];
     const Layout2 L = make_layout2<T>(R, p.D, DIRECT);
     T *bin = reinterpret_cast<T *>(smem2 + L.off_in);
     float *uf = reinterpret_cast<float *>(smem2 + (sizeof(T) == 4 ? L.off_in : L.off_uf));
-    float2 *AB = reinterpret_cast<float2 *>(smem2 + L.off_ab);
+    float *A = reinterpret_cast<float *>(smem2 + L.off_ab);
     float *Ua = reinterpret_cast<float *>(smem2 + L.off_ua);
     float *Ub = reinterpret_cast<float *>(smem2 + L.off_ub);
     const uint32_t bar = smem_u32(smem2 + L.bytes - 16);
@@ -438,7 +444,10 @@ __global__ void __launch_bounds__(NT, 2) osbf_fwd2(const __grid_constant__ CUten
             const int puin = j == 1 ? pu0 : L.PU;
             float *Uout = (j & 1) ? Ua : Ub;
             const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
-            pass_v2<R>(Uin, puin, AB, L.P2, RH, RW);
+            if (DIRECT)
+                pass_v2<R, TH + 2 * R>(Uin, puin, A, L.P2, RH, RW);
+            else
+                pass_v2<R, 0>(Uin, puin, A, L.P2, RH, RW);
             __syncthreads();
             Geom2 g;
             g.RHo = RH - 2 * R;
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(NT, 2) osbf_fwd2(const __grid_constant__ CUten
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, AB, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
