@@ -126,12 +126,19 @@ osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, in
 osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps,
                                  int N, int C, int H, int W, int r, int iters, void *stream);
 
+/* Row pitch, in float32 elements, of the padded frames the library stores
+ * (checkpoints): (W + 2r) rounded up to a multiple of 32. */
+int osbf_frame_pitch(int W, int r);
+
 /*
- * Backward from checkpoints: instead of every pass's map, the forward kept the
- * padded frame before every `interval`-th pass (ceil(iters/interval) frames of
- * N*C x (H+2r) x (W+2r) float32, frame k = state before pass k*interval, as written by
- * osbf_filter_checkpointed()).  Each segment's maps are recomputed from its
- * checkpoint into context workspace, then the segment is back-propagated.
+ * Checkpointed forward / backward (float32): instead of every pass's map, the
+ * forward keeps the padded frame before every `interval`-th pass: K = ceil(iters /
+ * interval) frames, each N*C x (H+2r) rows of osbf_frame_pitch(W, r) floats (frame k is
+ * the state before pass k*interval; frame 0 is the replicate-padded input).  The
+ * backward recomputes each segment's selection maps from its checkpoint into context
+ * workspace (interval x N*C x (H+2r) x (W+2r) bytes) and back-propagates the segment,
+ * last segment first.  Memory: K frames instead of iters maps.
+ * Returns OSBF_EINVAL for interval <= 0 and the argument errors of osbf_filter().
  */
 osbf_status osbf_filter_checkpointed(osbf_ctx *ctx, const float *in, float *out, float *checkpoints, int interval,
                                      int N, int C, int H, int W, int r, int iters, void *stream);
@@ -148,22 +155,39 @@ typedef struct {
 
 /*
  * Filter `njobs` independent images of different sizes, radii and pass counts in
- * one persistent launch (a device-side queue of tiles; a job's next fused group
- * starts once its previous group has finished), replayed from a CUDA graph that
- * the context caches per job signature.  Equivalent to one osbf_filter() per job
- * (float32, paper tie order).  Returns OSBF_ETIMEOUT if a bounded device-side
- * wait gave up (the outputs are then undefined); the context stays usable.
+ * one persistent launch (a device-side queue of (job, fused pass group, tile) items
+ * in group-round order; an item starts once its job's previous group has finished),
+ * replayed from a CUDA graph that the context caches per job signature (sizes,
+ * radii, pass counts and pointers).  Equivalent to one osbf_filter() per job
+ * (float32, paper tie order) up to float32 summation order.  Jobs with r = 0 or
+ * iters = 0 are copies; jobs with r > 8 run as separate filter calls.  Synchronous.
+ * Returns OSBF_EINVAL for a bad job (null pointer, non-positive size, in == out),
+ * OSBF_ETIMEOUT if a bounded device-side wait gave up (outputs then undefined; the
+ * context stays usable).
  */
 osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream);
 
+/* Per-image latency of the last osbf_filter_batched() call: for each job of its
+ * persistent launch (jobs with 1 <= r <= 8 and iters >= 1, in job order), the
+ * nanoseconds from the first CTA's start to the end of that job's last tile.  Returns
+ * the number of values written to ns (at most cap).  Synchronous. */
+int osbf_batched_latencies(osbf_ctx *ctx, unsigned long long *ns, int cap);
+
 /* Tune the fused depth for (dtype, r) on an H x W x planes problem by timing the
- * candidates on the device (synchronous); later calls with depth 0 use it. */
+ * candidates on the device (synchronous); later calls with depth 0 -- the plain,
+ * checkpointed and batched forms -- use it. */
 osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int iters);
 
 /* Synchronise the context's device and report whether any kernel of this context
  * gave up a bounded device-side wait since the last check (OSBF_ETIMEOUT; the
  * outputs of that call are undefined), then clear the record.  OSBF_OK otherwise. */
 osbf_status osbf_check(osbf_ctx *ctx);
+
+/* Bound, in nanoseconds, of the batched launch's device-side dependency wait (0 =
+ * the default of 2 s).  A smaller bound makes a batched call fail fast with
+ * OSBF_ETIMEOUT instead of waiting; it exists so that the timeout path can be
+ * exercised without any fault. */
+osbf_status osbf_set_wait_timeout(osbf_ctx *ctx, unsigned long long ns);
 
 /* Number of kernel launches the last filter call on `ctx` enqueued. */
 int osbf_last_launch_count(const osbf_ctx *ctx);

@@ -28,6 +28,7 @@ struct osbf_ctx {
     std::map<std::tuple<int, int, int>, int> tuned;  // (dtype, r, size class) -> depth
     void *batch_state = nullptr;                     // owned by the batched launcher
     unsigned int *err_word = nullptr;                // device: bit 0 = a bounded device wait gave up
+    unsigned long long wait_ns = 0;                  // bound of the batched dependency wait (0 = default)
 };
 
 // implemented in osbf_bwd_api.cu / osbf_batched.cu
@@ -397,6 +398,12 @@ const char *osbf_last_error(const osbf_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 int osbf_last_launch_count(const osbf_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
 
+osbf_status osbf_set_wait_timeout(osbf_ctx *ctx, unsigned long long ns) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->wait_ns = ns;
+    return OSBF_OK;
+}
+
 osbf_status osbf_check(osbf_ctx *ctx) {
     if (!ctx) return OSBF_EINVAL;
     DeviceGuard g(ctx->device);
@@ -577,12 +584,21 @@ osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *gr
 
 // accessors for the other translation units
 unsigned int *osbf_ctx_err_word(osbf_ctx *ctx) { return ctx->err_word; }
+unsigned long long osbf_ctx_wait_ns(const osbf_ctx *ctx) { return ctx->wait_ns; }
+int osbf_ctx_tuned_depth(osbf_ctx *ctx, osbf_dtype dt, int r, long long pixels) {
+    auto it = ctx->tuned.find(std::make_tuple((int)dt, r, size_class(pixels)));
+    return it != ctx->tuned.end() ? it->second : default_depth(r, dt);
+}
 void *osbf_ctx_workspace(osbf_ctx *ctx, int slot, size_t bytes, osbf_status *st) {
     *st = ensure(ctx, &ctx->ws[slot], &ctx->ws_bytes[slot], bytes);
     return *st == OSBF_OK ? ctx->ws[slot] : nullptr;
 }
 osbf_status osbf_ctx_fail(osbf_ctx *ctx, osbf_status code, const char *msg) { return fail(ctx, code, "%s", msg); }
 void osbf_ctx_count_launches(osbf_ctx *ctx, int n) { ctx->last_launches += n; }
+void osbf_ctx_reset_launches(osbf_ctx *ctx) {
+    ctx->last_launches = 0;
+    ctx->err.clear();
+}
 int osbf_ctx_sms(const osbf_ctx *ctx) { return ctx->sms; }
 int osbf_ctx_device(const osbf_ctx *ctx) { return ctx->device; }
 void **osbf_ctx_batch_state(osbf_ctx *ctx) { return &ctx->batch_state; }

@@ -1,11 +1,448 @@
-// Batched persistent launch (placeholder until the persistent kernel lands).
+// Batched form: many single-plane float32 images of different sizes, radii and pass
+// counts in ONE persistent launch, replayed from a CUDA graph cached per job signature.
+//
+// Work items are (job, pass group, tile), listed round by round: every job's group-0
+// tiles, then every job's group-1 tiles, and so on.  CTAs take items in that order from
+// a global counter; an item of group g first waits until all tiles of its job's group
+// g-1 are done (a per-(job, group) counter).  Every item listed before it has already
+// been taken by a resident CTA, so the wait always ends; it is bounded all the same
+// (a limit of 2 s, after which the kernel records an error that osbf_filter_batched
+// returns as OSBF_ETIMEOUT).  The sweep code is the forward's (osbf_fwd2.cuh), selected
+// per item by a switch on the radius; loads are plain 16-byte L2 loads (each job has its
+// own buffers, so no per-job tensor maps are needed).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
 #include "osbf.h"
+#include "osbf_fwd2.cuh"
 #include "osbf_internal.h"
 
 osbf_status osbf_ctx_fail(osbf_ctx *ctx, osbf_status code, const char *msg);
+void osbf_ctx_count_launches(osbf_ctx *ctx, int n);
+void osbf_ctx_reset_launches(osbf_ctx *ctx);
+int osbf_ctx_sms(const osbf_ctx *ctx);
+int osbf_ctx_device(const osbf_ctx *ctx);
+void **osbf_ctx_batch_state(osbf_ctx *ctx);
+int osbf_ctx_tuned_depth(osbf_ctx *ctx, osbf_dtype dt, int r, long long pixels);
+unsigned long long osbf_ctx_wait_ns(const osbf_ctx *ctx);
+osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int in_pitch, void *out, int out_is_frame,
+                             int out_pitch, int P, int H, int W, int r, int iters, osbf_dtype dtype, int depth,
+                             int tie, uint8_t *maps, int maps_iter0, long long maps_iter_stride, cudaStream_t s);
 
-void osbf_batched_free(osbf_ctx *) {}
+namespace osbf {
+namespace batched {
 
-extern "C" osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *, int, void *) {
-    return osbf_ctx_fail(ctx, OSBF_EUNSUPPORTED, "batched launch not built yet");
+constexpr int kMaxR = 8;  // radii served by the persistent launch (larger ones run per job)
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+struct Job {
+    const float *in;
+    float *out;
+    float *frame[2];
+    int H, W, FH, FW, FWp, R, D, iters, ngroups, tiles_x, ntiles, cnt_base;
+};
+
+struct Params {
+    unsigned long long wait_ns;  // bound of the dependency wait
+    const Job *jobs;
+    const int4 *items;  // (job, group, tile, -)
+    int nitems;
+    int *next;          // item counter
+    int *done;          // tiles finished per (job, group)
+    unsigned int *err;
+    unsigned long long *t_done;  // per job: globaltimer when its last tile finished
+    unsigned long long *t_start;
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
+
+// U^0 region of the tile into shared memory: the replicate-padded input (group 0) or the
+// job's previous frame (later groups; L2 loads, since another SM wrote it), zero outside.
+__device__ void load_region(const Job &jb, int g, const v2::Layout2 &L, float *U0, int ty0, int tx0) {
+    const int fy0 = ty0 - L.EY, fx0 = tx0 - L.EX;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (g == 0) {
+        for (int y = warp; y < L.RH0; y += v2::NT / 32) {
+            const int fy = fy0 + y;
+            const bool yin = (unsigned)fy < (unsigned)jb.FH;
+            const float *srow = jb.in + (long long)min(max(fy - jb.R, 0), jb.H - 1) * jb.W;
+            for (int x = lane; x < L.BX; x += 32) {
+                const int fx = fx0 + x;
+                float v = 0.f;
+                if (yin && (unsigned)fx < (unsigned)jb.FW) v = __ldg(srow + min(max(fx - jb.R, 0), jb.W - 1));
+                U0[y * L.BX + x] = v;
+            }
+        }
+    } else {
+        const float *src = jb.frame[(g - 1) & 1];
+        const int nv = L.BX / 4;
+        for (int i = threadIdx.x; i < L.RH0 * nv; i += v2::NT) {
+            const int y = i / nv, x = (i % nv) * 4;
+            const int fy = fy0 + y, fx = fx0 + x;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((unsigned)fy < (unsigned)jb.FH && fx >= 0 && fx < jb.FW) {
+                v = __ldcg(reinterpret_cast<const float4 *>(src + (long long)fy * jb.FWp + fx));
+                if (fx + 1 >= jb.FW) v.y = 0.f;
+                if (fx + 2 >= jb.FW) v.z = 0.f;
+                if (fx + 3 >= jb.FW) v.w = 0.f;
+            }
+            *reinterpret_cast<float4 *>(U0 + y * L.BX + x) = v;
+        }
+    }
+}
+
+template <int R>
+__device__ void process(const Job &jb, int g, int tile, unsigned char *smem) {
+    const int D = g == jb.ngroups - 1 ? jb.iters - g * jb.D : jb.D;
+    const v2::Layout2 L = v2::make_layout2<float>(R, D);
+    float *U0 = reinterpret_cast<float *>(smem + L.off_in);
+    float *A = reinterpret_cast<float *>(smem + L.off_ab);
+    float *Ua = reinterpret_cast<float *>(smem + L.off_ua);
+    float *Ub = reinterpret_cast<float *>(smem + L.off_ub);
+    const int ty0 = (tile / jb.tiles_x) * v2::TH, tx0 = (tile % jb.tiles_x) * v2::TW;
+    load_region(jb, g, L, U0, ty0, tx0);
+    __syncthreads();
+    const bool interior =
+        ty0 - L.EY >= 0 && tx0 - L.EX >= 0 && ty0 + v2::TH + L.EY <= jb.FH && tx0 + v2::TW + L.EX <= jb.FW;
+    for (int j = 1; j <= D; ++j) {
+        const float *Uin = j == 1 ? U0 : ((j & 1) ? Ub : Ua);
+        const int puin = j == 1 ? L.BX : L.PU;
+        float *Uout = (j & 1) ? Ua : Ub;
+        const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
+        v2::pass_v2<R, 0>(Uin, puin, A, L.P2, RH, RW);
+        __syncthreads();
+        v2::Geom2 gm;
+        gm.RHo = RH - 2 * R;
+        gm.RWo = RW - 2 * R;
+        gm.fy0 = ty0 - (L.EY - j * R);
+        gm.fx0 = tx0 - (L.EX - j * R);
+        gm.FH = jb.FH;
+        gm.FW = jb.FW;
+        gm.iy0 = gm.iy1 = gm.ix0 = gm.ix1 = 0;
+        v2::pass_h2<R, float, false, false, false>(Uin, puin, R, A, L.P2, Uout, L.PU, nullptr, 0, gm, nullptr);
+        __syncthreads();
+        if (j < D && !interior) {
+            v2::zero_outside(Uout, L.PU, gm.RHo, gm.RWo, gm.fy0, gm.fx0, jb.FH, jb.FW);
+            __syncthreads();
+        }
+    }
+    const float *UD = (D & 1) ? Ua : Ub;
+    const int cx = L.EX - D * R;
+    if (g < jb.ngroups - 1) {
+        float *dst = jb.frame[g & 1];
+        for (int i = threadIdx.x; i < v2::TH * v2::TW; i += v2::NT) {
+            const int y = i / v2::TW, x = i % v2::TW;
+            const int fy = ty0 + y, fx = tx0 + x;
+            if (fy < jb.FH && fx < jb.FW) dst[(long long)fy * jb.FWp + fx] = UD[y * L.PU + cx + x];
+        }
+    } else {
+        for (int i = threadIdx.x; i < v2::TH * v2::TW; i += v2::NT) {
+            const int y = i / v2::TW, x = i % v2::TW;
+            const int oy = ty0 + y - jb.R, ox = tx0 + x - jb.R;
+            if (oy >= 0 && oy < jb.H && ox >= 0 && ox < jb.W) jb.out[(long long)oy * jb.W + ox] = UD[y * L.PU + cx + x];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
+    extern __shared__ __align__(128) unsigned char bsmem[];
+    __shared__ int s_item;
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        atomicMin(p.t_start, now_ns());
+        s_fail = 0;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(p.next, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= p.nitems) break;
+        const int4 it = p.items[item];
+        const Job jb = p.jobs[it.x];
+        const int g = it.y;
+        if (threadIdx.x == 0 && g > 0) {
+            // the job's previous group must be complete (bounded wait)
+            const volatile int *cnt = p.done + jb.cnt_base + g - 1;
+            const unsigned long long t0 = now_ns();
+            while (*cnt < jb.ntiles) {
+                if (now_ns() - t0 > p.wait_ns) {
+                    atomicOr(p.err, 1u);
+                    s_fail = 1;
+                    break;
+                }
+                __nanosleep(256);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_fail) break;
+        switch (jb.R) {
+        case 1: process<1>(jb, g, it.z, bsmem); break;
+        case 2: process<2>(jb, g, it.z, bsmem); break;
+        case 3: process<3>(jb, g, it.z, bsmem); break;
+        case 4: process<4>(jb, g, it.z, bsmem); break;
+        case 5: process<5>(jb, g, it.z, bsmem); break;
+        case 6: process<6>(jb, g, it.z, bsmem); break;
+        case 7: process<7>(jb, g, it.z, bsmem); break;
+        default: process<8>(jb, g, it.z, bsmem); break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // this tile's results are visible before it is counted
+            const int prev = atomicAdd(p.done + jb.cnt_base + g, 1);
+            if (prev + 1 == jb.ntiles && g == jb.ngroups - 1) p.t_done[it.x] = now_ns();
+        }
+    }
+}
+
+}  // namespace batched
+}  // namespace osbf
+
+using namespace osbf;
+
+namespace {
+
+struct Planned {
+    cudaGraphExec_t exec = nullptr;
+    char *arena = nullptr;
+    unsigned int *err = nullptr;
+    unsigned long long *t_done = nullptr, *t_start = nullptr;
+    int njobs = 0;
+};
+
+struct BatchState {
+    std::map<std::vector<long long>, Planned> plans;  // job signature -> graph and arena
+    const Planned *last = nullptr;                    // for osbf_batched_latencies()
+};
+
+BatchState *state(osbf_ctx *ctx) {
+    void **slot = osbf_ctx_batch_state(ctx);
+    if (!*slot) *slot = new BatchState();
+    return (BatchState *)*slot;
+}
+
+}  // namespace
+
+void osbf_batched_free(osbf_ctx *ctx) {
+    void **slot = osbf_ctx_batch_state(ctx);
+    if (!*slot) return;
+    BatchState *st = (BatchState *)*slot;
+    for (auto &kv : st->plans) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaFree(kv.second.arena);
+    }
+    delete st;
+    *slot = nullptr;
+}
+
+extern "C" {
+
+osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream) {
+    if (!ctx) return OSBF_EINVAL;
+    osbf_ctx_reset_launches(ctx);
+    if (njobs < 0 || (njobs > 0 && !jobs)) return osbf_ctx_fail(ctx, OSBF_EINVAL, "bad job list");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int j = 0; j < njobs; ++j) {
+        const osbf_job &q = jobs[j];
+        if (!q.in || !q.out || q.H <= 0 || q.W <= 0 || q.r < 0 || q.iters < 0)
+            return osbf_ctx_fail(ctx, OSBF_EINVAL, "bad job");
+        if (q.r > OSBF_MAX_RADIUS) return osbf_ctx_fail(ctx, OSBF_EUNSUPPORTED, "job radius exceeds OSBF_MAX_RADIUS");
+        if (q.in == q.out) return osbf_ctx_fail(ctx, OSBF_EINVAL, "job in and out alias");
+    }
+    BatchState *bs = state(ctx);
+
+    // the persistent launch takes jobs with 1 <= r <= 8 and iters >= 1; the rest run alone
+    std::vector<int> pj;
+    std::vector<long long> sig;
+    sig.push_back(njobs);
+    sig.push_back((long long)osbf_ctx_wait_ns(ctx));
+    for (int j = 0; j < njobs; ++j) {
+        const osbf_job &q = jobs[j];
+        if (q.r == 0 || q.iters == 0) {
+            if (cudaMemcpyAsync(q.out, q.in, sizeof(float) * (size_t)q.H * q.W, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+                return osbf_ctx_fail(ctx, OSBF_ECUDA, "copy failed");
+        } else if (q.r > batched::kMaxR) {
+            osbf_status e = osbf_forward_run(ctx, q.in, 0, 0, q.out, 0, 0, 1, q.H, q.W, q.r, q.iters, OSBF_F32, 0, 0,
+                                             nullptr, 0, 0, s);
+            if (e) return e;
+        } else {
+            pj.push_back(j);
+            sig.insert(sig.end(), {(long long)(uintptr_t)q.in, (long long)(uintptr_t)q.out, q.H, q.W, q.r, q.iters,
+                                   osbf_ctx_tuned_depth(ctx, OSBF_F32, q.r, (long long)q.H * q.W)});
+        }
+    }
+    if (pj.empty()) return OSBF_OK;
+
+    auto git = bs->plans.find(sig);
+    if (git == bs->plans.end()) {
+        // ---- plan: jobs, items in round order, counters, arena ----
+        std::vector<batched::Job> hj(pj.size());
+        size_t frame_floats = 0;
+        int cnt = 0, max_groups = 0;
+        size_t smem = 0;
+        for (size_t k = 0; k < pj.size(); ++k) {
+            const osbf_job &q = jobs[pj[k]];
+            batched::Job &b = hj[k];
+            b.in = q.in;
+            b.out = q.out;
+            b.H = q.H;
+            b.W = q.W;
+            b.R = q.r;
+            b.FH = q.H + 2 * q.r;
+            b.FW = q.W + 2 * q.r;
+            b.FWp = (b.FW + 31) / 32 * 32;
+            b.iters = q.iters;
+            int D = osbf_ctx_tuned_depth(ctx, OSBF_F32, q.r, (long long)q.H * q.W);
+            while (D > 1 && (size_t)v2::make_layout2<float>(q.r, D).bytes > 200 * 1024) --D;
+            if (D > q.iters) D = q.iters;
+            b.D = D;
+            b.ngroups = (q.iters + D - 1) / D;
+            b.tiles_x = (b.FW + v2::TW - 1) / v2::TW;
+            b.ntiles = b.tiles_x * ((b.FH + v2::TH - 1) / v2::TH);
+            b.cnt_base = cnt;
+            cnt += b.ngroups;
+            max_groups = std::max(max_groups, b.ngroups);
+            frame_floats += (b.ngroups > 1 ? (b.ngroups > 2 ? 2 : 1) : 0) * (size_t)b.FH * b.FWp;
+            for (int g = 0; g < b.ngroups; ++g) {
+                const int Dg = g == b.ngroups - 1 ? q.iters - g * D : D;
+                smem = std::max(smem, (size_t)v2::make_layout2<float>(q.r, Dg).bytes);
+            }
+        }
+        std::vector<int4> items;
+        for (int g = 0; g < max_groups; ++g)
+            for (size_t k = 0; k < hj.size(); ++k)
+                if (g < hj[k].ngroups)
+                    for (int t = 0; t < hj[k].ntiles; ++t) items.push_back(make_int4((int)k, g, t, 0));
+        // arena: jobs | items | next | counters | err | t_done | t_start | frames
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            const size_t o = off;
+            off += (bytes + 255) & ~(size_t)255;
+            return o;
+        };
+        const size_t o_jobs = take(sizeof(batched::Job) * hj.size());
+        const size_t o_items = take(sizeof(int4) * items.size());
+        const size_t o_next = take(sizeof(int));
+        const size_t o_done = take(sizeof(int) * (size_t)cnt);
+        const size_t o_err = take(sizeof(unsigned int));
+        const size_t o_tdone = take(sizeof(unsigned long long) * hj.size());
+        const size_t o_tstart = take(sizeof(unsigned long long));
+        const size_t o_frames = take(sizeof(float) * frame_floats);
+        char *arena = nullptr;
+        if (cudaMalloc(&arena, off) != cudaSuccess) {
+            cudaGetLastError();
+            return osbf_ctx_fail(ctx, OSBF_ENOMEM, "batched arena allocation failed");
+        }
+        float *fr = (float *)(arena + o_frames);
+        for (auto &b : hj) {
+            b.frame[0] = b.frame[1] = nullptr;
+            if (b.ngroups > 1) {
+                b.frame[0] = fr;
+                fr += (size_t)b.FH * b.FWp;
+            }
+            if (b.ngroups > 2) {
+                b.frame[1] = fr;
+                fr += (size_t)b.FH * b.FWp;
+            }
+        }
+        if (cudaMemcpy(arena + o_jobs, hj.data(), sizeof(batched::Job) * hj.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(arena + o_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            cudaFree(arena);
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, "batched plan upload failed");
+        }
+        batched::Params p;
+        p.wait_ns = osbf_ctx_wait_ns(ctx);
+        if (p.wait_ns == 0) p.wait_ns = batched::kWaitNs;
+        p.jobs = (const batched::Job *)(arena + o_jobs);
+        p.items = (const int4 *)(arena + o_items);
+        p.nitems = (int)items.size();
+        p.next = (int *)(arena + o_next);
+        p.done = (int *)(arena + o_done);
+        p.err = (unsigned int *)(arena + o_err);
+        p.t_done = (unsigned long long *)(arena + o_tdone);
+        p.t_start = (unsigned long long *)(arena + o_tstart);
+        if (cudaFuncSetAttribute(batched::osbf_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess) {
+            cudaFree(arena);
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, "shared memory attribute");
+        }
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched::osbf_batched_kernel, v2::NT, smem);
+        if (occ < 1) occ = 1;
+        int grid = occ * osbf_ctx_sms(ctx);  // all CTAs resident: every wait is on a running CTA
+        if (grid > (int)items.size()) grid = (int)items.size();
+
+        // ---- capture: reset the counters, then the persistent launch ----
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaFree(arena);
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, "stream creation failed");
+        }
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaMemsetAsync(arena + o_next, 0, o_tstart - o_next, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(arena + o_tstart, 0xff, sizeof(unsigned long long), cs);
+        if (e == cudaSuccess) {
+            batched::osbf_batched_kernel<<<grid, v2::NT, smem, cs>>>(p);
+            e = cudaGetLastError();
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            cudaFree(arena);
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, cudaGetErrorString(e));
+        }
+        Planned pl;
+        pl.exec = exec;
+        pl.arena = arena;
+        pl.err = p.err;
+        pl.t_done = p.t_done;
+        pl.t_start = p.t_start;
+        pl.njobs = (int)hj.size();
+        git = bs->plans.emplace(sig, pl).first;
+    }
+    const Planned &pl = git->second;
+    bs->last = &pl;
+    cudaError_t e = cudaGraphLaunch(pl.exec, s);
+    if (e != cudaSuccess) return osbf_ctx_fail(ctx, OSBF_ECUDA, cudaGetErrorString(e));
+    osbf_ctx_count_launches(ctx, 1);
+    // the bounded waits report through the arena's error word
+    unsigned int w = 0;
+    if (cudaMemcpyAsync(&w, pl.err, sizeof w, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return osbf_ctx_fail(ctx, OSBF_ECUDA, "batched launch failed");
+    if (w) return osbf_ctx_fail(ctx, OSBF_ETIMEOUT, "a batched item waited too long for its previous pass group");
+    return OSBF_OK;
+}
+
+// Per-image latency of the last osbf_filter_batched() call on `ctx` (see osbf.h).
+int osbf_batched_latencies(osbf_ctx *ctx, unsigned long long *ns, int cap) {
+    if (!ctx || !ns || cap <= 0) return 0;
+    BatchState *bs = state(ctx);
+    const Planned *pl = bs->last;
+    if (!pl || pl->njobs == 0) return 0;
+    std::vector<unsigned long long> t(pl->njobs);
+    unsigned long long t0 = 0;
+    if (cudaMemcpy(t.data(), pl->t_done, sizeof(unsigned long long) * pl->njobs, cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(&t0, pl->t_start, sizeof t0, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return 0;
+    const int n = pl->njobs < cap ? pl->njobs : cap;
+    for (int i = 0; i < n; ++i) ns[i] = t[i] > t0 ? t[i] - t0 : 0;
+    return n;
+}
+
+}  // extern "C"

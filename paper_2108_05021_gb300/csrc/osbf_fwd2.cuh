@@ -68,6 +68,7 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     off = align128(off + L.in_bytes);
     L.off_uf = off;  // float copy of the input (16-bit storage only)
     if (sizeof(T) != 4) off = align128(off + L.RH0 * L.PU * 4);
+
     L.off_ab = off;
     off = align128(off + (L.RH0 - R) * L.P2 * 4);
     L.off_ua = off;
@@ -116,6 +117,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "[%5];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
+}
+
+// Pull a box of the tensor into L2 ahead of its load (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap *map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -179,14 +188,16 @@ template <> __device__ __forceinline__ void cvt_store4<__nv_bfloat16>(__nv_bfloa
 // ----------------------------------------------------------------------------------
 template <int R, int NRH>
 __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float *__restrict__ A, int pa, int RH_rt,
-                                        int RW) {
+                                        int RW, float *__restrict__ uc = nullptr) {
     constexpr int P = R + 1;
     const int RH = NRH > 0 ? NRH : RH_rt;
+    const int pu_c = pa;  // the central-rows copy has the same pitch as A
     const int npairs = (RW + 1) >> 1;
     for (int item = threadIdx.x; item < npairs; item += NT) {
         const int c = item * 2;
         const float *col = U + c;
         float2 *acol = reinterpret_cast<float2 *>(A + c);
+        float2 *ucol = uc ? reinterpret_cast<float2 *>(uc + c) : nullptr;
         float2 ring[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) ring[k] = make_float2(0.f, 0.f);
@@ -203,6 +214,7 @@ __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, flo
                 ring[k] = v;
             }
             if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
+            if (NRH > 0 && ucol && s >= R && s < R + TH) ucol[(s - R) * (pu_c >> 1)] = v;
         };
         if (NRH > 0) {
 #pragma unroll
@@ -252,11 +264,12 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
 // -- DIRECT -- four results at a time straight into the destination frame in global
 // memory (storage type T, 16- or 8-byte stores, rows and columns outside the frame skipped).
 template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT>
-__device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, const float *__restrict__ A, int pa,
-                                        float *__restrict__ Uout, int pu_out, T *__restrict__ gdst,
-                                        long long gpitch, const Geom2 &g, uint8_t *__restrict__ mplane) {
-    constexpr int P = (R + 1 + 3) & ~3;  // ring period: >= R+1, a multiple of 4
-    constexpr int NS = SW + 2 * R;       // sweep steps of one segment (2R of warm-up)
+__device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, int urow0,
+                                        const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
+                                        T *__restrict__ gdst, long long gpitch, const Geom2 &g,
+                                        uint8_t *__restrict__ mplane) {
+    constexpr int P = R + 1;         // ring period (the sweep is fully unrolled, so any period is static)
+    constexpr int NS = SW + 2 * R;   // sweep steps of one segment (2R of warm-up)
     constexpr float iq = 1.0f / float((R + 1) * (R + 1));
     constexpr float ih = 1.0f / float((R + 1) * (2 * R + 1));
     const float2 iq2 = make_float2(iq, iq), ih2 = make_float2(ih, ih);
@@ -271,13 +284,13 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const int xs = seg * SW;
         const float4 *arow = reinterpret_cast<const float4 *>(A + yr * pa + xs);        // a: up column sums
         const float4 *brow = reinterpret_cast<const float4 *>(A + (yr + R) * pa + xs);  // b: down column sums
-        const float4 *urow = reinterpret_cast<const float4 *>(Uin + (yr + R) * pu_in + xs);
+        const float4 *urow = reinterpret_cast<const float4 *>(Uin + (yr + urow0) * pu_in + xs);
         float4 *orow = reinterpret_cast<float4 *>(Uout + yr * pu_out + xs);
         const int fy = g.fy0 + yo;
         const bool row_store = DIRECT ? (row_ok && (unsigned)fy < (unsigned)g.FH) : row_ok;
         T *grow = DIRECT ? gdst + (long long)(row_store ? fy : 0) * gpitch + g.fx0 + xs : nullptr;
         const bool row_map = MAPS && row_ok && (unsigned)fy < (unsigned)g.FH && yo >= g.iy0 && yo < g.iy1;
-        float ra[P], rb[P], ru[P], hu[P];
+        float ra[P], rb[P], ru[P], h6[P];  // raw a, b, U; and N6 sums (N5 at x is N6 at x - r)
         float2 hab[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
@@ -299,7 +312,14 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 vu = urow[t >> 2];
             }
             const float a = f4get(va, t & 3), b = f4get(vb, t & 3), u = f4get(vu, t & 3);
-            if (R <= 3 || k == P - 1) {
+            if (t < R) {
+                // warm-up: no window is complete yet; only fill the rings
+                ra[k] = a;
+                rb[k] = b;
+                ru[k] = u;
+                continue;
+            }
+            if (R <= 3 || k == P - 1 || t == R) {
                 // direct sum over the ring's last R+1 entries (cheap for small r; resets
                 // the running sums' FP32 drift once per ring period for large r)
                 ra[k] = a;
@@ -323,16 +343,17 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 ru[k] = u;
             }
             hab[k] = ABL;
-            hu[k] = UL;
+            // N6 at the current column: the right half window of column x = t - R
+            const float n6 = (ABL.x + ABL.y) - UL;
+            h6[k] = n6;
             if (t >= 2 * R) {
                 const int sl = (k + P - R) % P;  // column x = t - R; (AL, BL) at x+R is current
                 const float2 ABx = hab[sl];      // (AL(x), BL(x)) = (N4, N1)
-                const float ULx = hu[sl];
                 const float ux = ru[sl];
                 const float2 nu = make_float2(-ux, -ux);
                 const float2 sum = add2(ABx, ABL);
-                const float2 s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);          // (N8, N7)
-                const float2 s56 = make_float2(ABx.x + ABx.y - ULx, ABL.x + ABL.y - UL);  // (N5, N6)
+                const float2 s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);  // (N8, N7)
+                const float2 s56 = make_float2(h6[sl], n6);  // N5(x) = N6(x - r) : left half of x
                 const float2 d41 = fma2(ABx, iq2, nu);
                 const float2 d32 = fma2(ABL, iq2, nu);  // (N3, N2) = (AL(x+r), BL(x+r))
                 const float2 d56 = fma2(s56, ih2, nu);
@@ -377,9 +398,10 @@ __device__ __forceinline__ void zero_outside(float *__restrict__ U, int pu, int 
 // destination frame (needs D == 1, EX == R and a frame destination); otherwise every
 // pass lands in shared memory and the tile interior is copied out at the end.
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
-__global__ void __launch_bounds__(NT, DIRECT ? (R <= 8 ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
     extern __shared__ __align__(128) unsigned char smem2[];
-    const Layout2 L = make_layout2<T>(R, p.D, DIRECT);
+    const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
+    const Layout2 L = make_layout2<T>(R, D, DIRECT);
     T *bin = reinterpret_cast<T *>(smem2 + L.off_in);
     float *uf = reinterpret_cast<float *>(smem2 + (sizeof(T) == 4 ? L.off_in : L.off_uf));
     float *A = reinterpret_cast<float *>(smem2 + L.off_ab);
@@ -401,16 +423,27 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 8 ? 4 : 3) : 2) osbf_fwd2(c
         const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
         tma_load_3d(smem_u32(bin), &src, tx0 - L.EX, ty0 - L.EY, plane, bar, (uint32_t)L.in_bytes);
     };
+    // L2 prefetch of a tile's box: issued one tile ahead of its shared-memory load, so
+    // that load is served from L2 instead of DRAM
+    auto warm = [&](int tile) {
+        const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
+        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
+        tma_prefetch_l2_3d(&src, tx0 - L.EX, ty0 - L.EY, plane);
+    };
     auto prefetch = [&](int tile) {
         const int next = tile + gridDim.x;
         if (next < p.ntiles && threadIdx.x == 0) {
             fence_proxy_async();
             issue(next);
+            if (next + (int)gridDim.x < p.ntiles) warm(next + gridDim.x);
         }
     };
 
     int tile = blockIdx.x;
-    if (tile < p.ntiles && threadIdx.x == 0) issue(tile);
+    if (tile < p.ntiles && threadIdx.x == 0) {
+        issue(tile);
+        if (tile + (int)gridDim.x < p.ntiles) warm(tile + gridDim.x);
+    }
     uint32_t phase = 0;
     for (; tile < p.ntiles; tile += gridDim.x) {
         const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
@@ -439,16 +472,24 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 8 ? 4 : 3) : 2) osbf_fwd2(c
         const bool interior = ty0 - L.EY >= 0 && tx0 - L.EX >= 0 && ty0 + TH + L.EY <= p.FH &&
                               tx0 + TW + L.EX <= p.FW;
         T *gdst = reinterpret_cast<T *>(p.dst) + (long long)plane * p.dst_plane;
-        for (int j = 1; j <= p.D; ++j) {
+        for (int j = 1; j <= D; ++j) {
             const float *Uin = j == 1 ? uf : ((j & 1) ? Ub : Ua);
             const int puin = j == 1 ? pu0 : L.PU;
             float *Uout = (j & 1) ? Ua : Ub;
             const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
+            // direct float32 kernels: pass V also copies the pixel rows of U, so the TMA box
+            // is dead after pass V and the next tile's load overlaps pass H
+            constexpr bool UCOPY = false;  // a central-row copy frees the box early but costs a CTA per SM
+            float *uc = reinterpret_cast<float *>(smem2 + L.off_uf);
             if (DIRECT)
-                pass_v2<R, TH + 2 * R>(Uin, puin, A, L.P2, RH, RW);
+                pass_v2<R, TH + 2 * R>(Uin, puin, A, L.P2, RH, RW, UCOPY ? uc : nullptr);
             else
                 pass_v2<R, 0>(Uin, puin, A, L.P2, RH, RW);
             __syncthreads();
+            if (UCOPY && !prefetched) {
+                prefetch(tile);
+                prefetched = true;
+            }
             Geom2 g;
             g.RHo = RH - 2 * R;
             g.RWo = RW - 2 * R;
@@ -464,13 +505,16 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 8 ? 4 : 3) : 2) osbf_fwd2(c
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            if (UCOPY)
+                pass_h2<R, T, TIE_APP, MAPS, DIRECT>(uc, L.P2, 0, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            else
+                pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
                 prefetched = true;
             }
-            if (!DIRECT && j < p.D && !interior) {
+            if (!DIRECT && j < D && !interior) {
                 zero_outside(Uout, L.PU, g.RHo, g.RWo, g.fy0, g.fx0, p.FH, p.FW);
                 __syncthreads();
             }
@@ -478,8 +522,8 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 8 ? 4 : 3) : 2) osbf_fwd2(c
         if (DIRECT) continue;  // results already in the destination frame
 
         // store the tile interior of U^D (row-wise, coalesced)
-        const float *UD = (p.D & 1) ? Ua : Ub;
-        const int cx = L.EX - p.D * R;
+        const float *UD = (D & 1) ? Ua : Ub;
+        const int cx = L.EX - D * R;
         if (!p.dst_is_output) {
             if ((cx & 3) == 0) {
                 for (int i = threadIdx.x; i < TH * (TW / 4); i += NT) {

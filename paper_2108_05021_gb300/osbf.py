@@ -82,6 +82,14 @@ def lib() -> ctypes.CDLL:
         L.osbf_filter_batched.restype = st
         L.osbf_autotune.argtypes = [vp, i, i, i, i, i, i]
         L.osbf_autotune.restype = st
+        L.osbf_frame_pitch.argtypes = [i, i]
+        L.osbf_frame_pitch.restype = i
+        L.osbf_check.argtypes = [vp]
+        L.osbf_check.restype = st
+        L.osbf_batched_latencies.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), i]
+        L.osbf_batched_latencies.restype = i
+        L.osbf_set_wait_timeout.argtypes = [vp, ctypes.c_ulonglong]
+        L.osbf_set_wait_timeout.restype = st
         _lib = L
     return _lib
 
@@ -214,12 +222,24 @@ def checkpoint_count(iters: int, interval: int) -> int:
     return (iters + interval - 1) // interval
 
 
+def frame_pitch(W: int, r: int) -> int:
+    return lib().osbf_frame_pitch(W, r)
+
+
+def check(device: int = 0) -> None:
+    """osbf_check: raise if a bounded device-side wait of this context gave up."""
+    ctx = context(device)
+    _check(lib().osbf_check(ctx), ctx)
+
+
 def filter_checkpointed(x: torch.Tensor, r: int, iters: int, interval: int):
-    """Forward that keeps a padded frame every `interval` passes; returns (out, checkpoints)."""
+    """Forward that keeps a padded frame every `interval` passes; returns (out, checkpoints).
+
+    checkpoints: K x N*C x (H+2r) x frame_pitch(W, r) float32 (the valid width is W + 2r)."""
     _require_cuda(x)
     N, C, H, W = _nchw(x)
-    ck = torch.empty((checkpoint_count(iters, interval), N * C, H + 2 * r, W + 2 * r), dtype=torch.float32,
-                     device=x.device)
+    ck = torch.empty((checkpoint_count(iters, interval), N * C, H + 2 * r, frame_pitch(W, r)),
+                     dtype=torch.float32, device=x.device)
     out = torch.empty_like(x)
     dev = x.device.index
     ctx = context(dev)
@@ -258,6 +278,19 @@ def batched(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequenc
     ctx = context(dev)
     _check(lib().osbf_filter_batched(ctx, jobs, n, _stream(dev)), ctx)
     return list(outputs)
+
+
+def set_wait_timeout(ns: int, device: int = 0) -> None:
+    """Bound of the batched launch's device-side dependency wait (0 = default 2 s)."""
+    ctx = context(device)
+    _check(lib().osbf_set_wait_timeout(ctx, int(ns)), ctx)
+
+
+def batched_latencies(n: int, device: int = 0) -> list:
+    """Per-image latencies (seconds) of the last batched call's persistent launch."""
+    buf = (ctypes.c_ulonglong * max(n, 1))()
+    k = lib().osbf_batched_latencies(context(device), buf, n)
+    return [buf[i] * 1e-9 for i in range(k)]
 
 
 def autotune(dtype: torch.dtype, planes: int, H: int, W: int, r: int, iters: int, device: int = 0) -> None:
