@@ -1,8 +1,8 @@
 """Throughput benchmark of the One-Sided Box Filter library on GB300.
 
-Workload: the plain float32 forward on 1 x 3 x 4096 x 4096 synthetic piecewise-constant
-+ noise images (40 rectangles, 20 triangles, sigma 0.05, each channel its own plane),
-r = 8, 30 passes.  A "step" is one full filter call (all 30 passes) on that batch.
+Headline workload: the plain float32 forward on 1 x 3 x 4096 x 4096 synthetic
+piecewise-constant + noise images (40 rectangles, 20 triangles, sigma 0.05, each channel
+its own plane), r = 8, 30 passes.  A "step" is one full filter call (all 30 passes).
 The inputs (201 MB) exceed the 129 MB L2, so no flush is needed between steps.
 
 Printed JSON line (rank 0):
@@ -14,8 +14,12 @@ Printed JSON line (rank 0):
   roofline     the forward tile kernel's algorithmic bytes (read + write of every frame
                pixel once per launch) per launch over its average launch time, against
                the measured HBM copy bandwidth;
-  cpu_baseline the CPU oracle on the host cores, on a bounded sample (one 1024 x 1024
-               crop of the same image, r = 8) -- a reported baseline, not the target.
+  cpu_baseline the CPU oracle on the host cores, on a bounded sample (a 1024 x 1024 crop
+               of the same image, r = 8) -- a reported baseline, not the target;
+  forms        the other forms against the plain one on the same GPU: forward+backward
+               (16x3x512^2, r=3, 5 passes), batched (256 images), float16 / bfloat16
+               storage (7680x4320x3, r=4, 30 passes, error against the FP64 oracle on a
+               sampled region), and the r x fused-depth sweep at 4096^2 x 3.
 
 `--impl reference` times the CPU oracle as the reference arm (bounded sample per step).
 Multi-GPU: `torchrun --nproc-per-node N bench.py --gpus N`: every rank filters its own
@@ -43,6 +47,9 @@ N_, C_, H_, W_, R_, ITERS_ = 1, 3, 4096, 4096, 8, 30
 WORKLOAD = "osbf forward, 1x3x4096x4096 float32, r=8, 30 passes, piecewise-constant+noise (sigma 0.05)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) of one forward launch of the headline workload, from one ncu
+# capture of that launch (to be reset to None whenever the kernel changes)
+TRAFFIC_PER_LAUNCH = 358.6e6
 
 
 def hbm_peak():
@@ -60,6 +67,22 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, pg, device=None) -> float:
+    """Max of a scalar over all ranks (identity without a process group)."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -70,6 +93,7 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -81,7 +105,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -94,7 +117,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        for l in self.lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -159,6 +182,132 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------------------
+# the other forms, each against the plain form on the same GPU
+# --------------------------------------------------------------------------------------
+def _time(fn, steps, warmup=3):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps * 1e-3  # seconds per step
+
+
+def form_fwd_bwd(dev):
+    """16 x 3 x 512^2, r = 3, 5 passes; loss = MSE(osbf(noisy), clean)."""
+    import torch
+
+    from paper_2108_05021_gb300 import osbf, synth
+
+    N, C, H, W, r, it = 16, 3, 512, 512, 3, 5
+    x = torch.from_numpy(synth.piecewise_stack(N, C, H, W, seed=50, sigma=0.05)).to(dev)
+    clean = torch.from_numpy(synth.piecewise_stack(N, C, H, W, seed=50, sigma=0.0)).to(dev)
+    maps = torch.empty(osbf.maps_shape(x, r, it), dtype=torch.uint8, device=dev)
+    out = torch.empty_like(x)
+    gin = torch.empty_like(x)
+
+    def fwd():
+        osbf.filter(x, r, it, out=out)
+
+    def fwd_bwd():
+        osbf.filter(x, r, it, maps=maps, out=out)
+        g = (2.0 / out.numel()) * (out - clean)
+        osbf.backward(g, maps, r, it, out=gin)
+
+    def fwd_bwd_ck():
+        y, ck = osbf.filter_checkpointed(x, r, it, 2)
+        g = (2.0 / y.numel()) * (y - clean)
+        osbf.backward_checkpointed(g, ck, r, it, 2)
+
+    units = N * C * H * W * it
+    t_f, t_fb, t_ck = _time(fwd, 20), _time(fwd_bwd, 20), _time(fwd_bwd_ck, 10)
+    return {"workload": "16x3x512x512 float32, r=3, 5 passes, MSE(osbf(noisy), clean)",
+            "fwd_mpix_iter_s": units / t_f / 1e6, "fwd_bwd_mpix_iter_s": units / t_fb / 1e6,
+            "fwd_bwd_checkpointed_k2_mpix_iter_s": units / t_ck / 1e6,
+            "fwd_bwd_time_over_fwd": t_fb / t_f}
+
+
+def form_batched(dev):
+    """256 images, H, W ~ U[64, 2048], r in {1,2,3,4,6,8}, passes ~ U[1, 30]."""
+    import torch
+
+    from paper_2108_05021_gb300 import osbf, synth
+
+    rng = np.random.default_rng(4)
+    ins, rs, its = [], [], []
+    for k in range(256):
+        H, W = (int(v) for v in rng.integers(64, 2049, size=2))
+        ins.append(torch.from_numpy(synth.piecewise_stack(1, 1, H, W, seed=2000 + k, sigma=0.05)[0, 0]).to(dev))
+        rs.append(int(rng.choice([1, 2, 3, 4, 6, 8])))
+        its.append(int(rng.integers(1, 31)))
+    outs = [torch.empty_like(t) for t in ins]
+    units = sum(t.numel() * i for t, i in zip(ins, its))
+
+    def batched():
+        osbf.batched(ins, rs, its, outputs=outs)
+
+    def plain():
+        for t, r, i, o in zip(ins, rs, its, outs):
+            osbf.filter(t, r, i, out=o)
+
+    t_b = _time(batched, 5, warmup=2)
+    lat = sorted(osbf.batched_latencies(256))
+    t_p = _time(plain, 3, warmup=1)
+    return {"workload": "256 float32 images, H,W~U[64,2048], r in {1,2,3,4,6,8}, passes~U[1,30]",
+            "batched_mpix_iter_s": units / t_b / 1e6, "plain_calls_mpix_iter_s": units / t_p / 1e6,
+            "batched_over_plain": t_p / t_b, "p50_latency_ms": 1e3 * lat[len(lat) // 2],
+            "p99_latency_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "total_pixel_iters": units}
+
+
+def form_precision(dev):
+    """7680 x 4320 x 3 stored as f32 / f16 / bf16, r = 4, 30 passes, sigma 0.03."""
+    import torch
+
+    import oracle
+    from paper_2108_05021_gb300 import osbf, synth
+
+    H, W, r, it = 4320, 7680, 4, 30
+    x32 = synth.piecewise_stack(1, 3, H, W, seed=3, sigma=0.03)
+    res = {"workload": "1x3x4320x7680, r=4, 30 passes, sigma 0.03"}
+    y0, x0, s = H // 2, W // 2, 48  # sampled output region of plane 0
+    for name, dt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
+        xin = x32 if name == "f32" else synth.round_to_storage(x32, name)
+        xt = torch.from_numpy(xin).to(dev).to(dt)
+        out = torch.empty_like(xt)
+        t = _time(lambda: osbf.filter(xt, r, it, out=out), 5)
+        got = out[0, 0, y0:y0 + s, x0:x0 + s].float().cpu().numpy()
+        ref = oracle.filter_region(xin[0, 0].astype(np.float64), r, it, y0, y0 + s, x0, x0 + s)
+        err = np.abs(got - ref)
+        res[name] = {"mpix_iter_s": 3 * H * W * it / t / 1e6, "max_abs_err_vs_fp64": float(err.max()),
+                     "mean_abs_err_vs_fp64": float(err.mean()), "err_sample": f"{s}x{s} at ({y0},{x0}), plane 0"}
+    return res
+
+
+def form_sweep(dev, x):
+    import torch
+
+    from paper_2108_05021_gb300 import osbf
+
+    out = torch.empty_like(x)
+    rows = []
+    for r in (1, 2, 4, 8, 16):
+        for D in (1, 2, 4, 8):
+            try:
+                t = _time(lambda: osbf.filter(x, r, ITERS_, depth=D, out=out), 5, warmup=2)
+            except osbf.OSBFError:
+                continue
+            rows.append({"r": r, "depth": D, "gpix_iter_s": x.numel() * ITERS_ / t / 1e9})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,6 +318,7 @@ def main():
     ap.add_argument("--r", type=int, default=R_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other forms (for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -214,24 +364,23 @@ def main():
         torch.cuda.synchronize(dev)
     if pg:
         pg.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), pg, dev)
     ms_step = ms / args.steps
     pix_iters = N_ * C_ * H_ * W_ * ITERS_
-    value = ws * pix_iters / (ms_step * 1e-3) / 1e6
+    value = whole_job_rate(pix_iters, ws, ms_step * 1e-3) / 1e6
 
-    # roofline of the forward tile kernel: every launch reads and writes each frame pixel once
+    # roofline of the forward tile kernel: every launch reads and writes each frame pixel
+    # once (the replicate-pad launch is one of the step's launches and is cheaper)
     FH, FW = H_ + 2 * r, W_ + 2 * r
     bytes_per_launch = 8.0 * N_ * C_ * FH * FW
     launch_ms = ms_step / max(launches_per_step, 1)
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_kind, "kernel": "osbf_fwd_tile",
-                "bytes_per_launch": bytes_per_launch, "launches_per_step": launches_per_step}
+                "traffic": TRAFFIC_PER_LAUNCH if r == R_ and args.depth in (0, 1) else None,
+                "peak_source": peak_kind, "kernel": "osbf_fwd2 (forward tile kernel)",
+                "bytes_per_launch": bytes_per_launch, "launches_per_step": launches_per_step,
+                "hbm_roofline_equiv_mpix_iter_s": peak * 1e9 / 8.0 / 1e6}
 
     e2e = None
     if not args.no_e2e:
@@ -243,13 +392,15 @@ def main():
         t0 = time.perf_counter()
         for _ in range(ne):
             osbf.filter_host(xh, r, ITERS_, out=oh, device=local)
-        dt = (time.perf_counter() - t0) / ne
-        if pg:
-            t = torch.tensor([dt], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * pix_iters / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes),
-               "d2h_bytes_per_step": int(x_np.nbytes), "ms_per_step": dt * 1e3, "api": "osbf_filter_host"}
+        dt = reduce_max((time.perf_counter() - t0) / ne, pg, dev)
+        e2e = {"value": whole_job_rate(pix_iters, ws, dt) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(x_np.nbytes),
+               "ms_per_step": dt * 1e3, "api": "osbf_filter_host"}
+
+    forms = None
+    if rank == 0 and ws == 1 and not args.no_forms:
+        forms = {"fwd_bwd": form_fwd_bwd(dev), "batched": form_batched(dev), "precision": form_precision(dev),
+                 "sweep_4096x3_30_passes": form_sweep(dev, x), "plain_mpix_iter_s": value}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -264,7 +415,7 @@ def main():
                            "depth": args.depth or "library", "l2": "inputs (201 MB) exceed L2; no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "forms": forms}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
