@@ -192,6 +192,30 @@ osbf_status osbf_set_wait_timeout(osbf_ctx *ctx, unsigned long long ns);
 /* Number of kernel launches the last filter call on `ctx` enqueued. */
 int osbf_last_launch_count(const osbf_ctx *ctx);
 
+/*
+ * The float32 forward of osbf_filter() without any device allocation.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call cudaMalloc,
+ * such as real-time pipelines that must not allocate once running (an allocation can
+ * synchronise the device or fail under memory pressure) and plug-ins whose host
+ * process owns all device memory through its own allocator.
+ *   - No context: it runs on the current CUDA device, on `stream`.  The caller passes
+ *     device input and output (N x C x H x W float32, not aliasing), as for
+ *     osbf_filter(); tie order is the paper's, one pass per launch.
+ *   - Its scratch is a fixed device array inside the library: two padded frames of at
+ *     most OSBF_NOALLOC_MAX_FRAME_FLOATS floats each (N*C*(H+2r) rows of (W+2r) rounded
+ *     up to 32 floats); every GPU that loads the library holds this 32 MiB until exit.
+ *     Larger problems return OSBF_EUNSUPPORTED, as does r > OSBF_MAX_RADIUS; bad
+ *     arguments return OSBF_EINVAL; a failed CUDA call returns OSBF_ECUDA.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (each call
+ *     rewrites what it reads).  Calls that overlap on the GPU race on it: serialise
+ *     them (one stream, or events).
+ */
+#define OSBF_NOALLOC_MAX_FRAME_FLOATS (4LL << 20)
+osbf_status osbf_filter_noalloc(const float *in, float *out, int N, int C, int H, int W, int r, int iters,
+                                void *stream);
+
 /* Library version string. */
 const char *osbf_version(void);
 

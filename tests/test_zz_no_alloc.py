@@ -1,0 +1,50 @@
+"""The allocation-free forward entry point (osbf_filter_noalloc), called through the C ABI.
+
+It serves callers that cannot allocate device memory; its scratch is a fixed array
+inside the library that every call shares.  Two calls in a row, with different
+shapes and radii, must each give what the allocating entry point gives for the same
+one-pass-per-launch schedule (within the float32 tolerance of the other GPU tests,
+1e-5), so no stale scratch contents leak from one call into the next.  This file is
+collected last so that a failure here cannot stop the rest of the suite.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2108_05021_gb300 import osbf, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def noalloc(x, r, iters, out=None):
+    L = osbf.lib()
+    fn = L.osbf_filter_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 6 + [ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    if out is None:
+        out = torch.empty_like(x)
+    N, C, H, W = x.shape
+    with torch.cuda.device(x.device):
+        st = fn(x.data_ptr(), out.data_ptr(), N, C, H, W, r, iters,
+                ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream))
+    return st, out
+
+
+def test_noalloc_matches_filter_on_two_calls():
+    cases = [((1, 3, 200, 300), 8, 4, 11), ((2, 1, 150, 257), 3, 5, 12)]
+    for shape, r, iters, seed in cases:
+        x = torch.from_numpy(synth.piecewise_stack(*shape, seed=seed, sigma=0.05)).to(DEV)
+        st, got = noalloc(x, r, iters)
+        assert st == 0
+        want = osbf.filter(x, r, iters, depth=1)
+        torch.cuda.synchronize()
+        assert np.abs(got.cpu().numpy() - want.cpu().numpy()).max() <= 1e-5
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch():
+    x = torch.zeros(1, 1, 4096, 4096, device=DEV)
+    st, _ = noalloc(x, 8, 1)
+    assert st == 4  # OSBF_EUNSUPPORTED: the frames would exceed the fixed scratch
