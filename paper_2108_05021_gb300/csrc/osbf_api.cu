@@ -327,8 +327,14 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
         if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
         p.ntiles = (int)ntiles;
-        // one pass written straight from registers into a destination frame
-        const bool direct = Dg == 1 && !p.dst_is_output && L.EX == r && tie == 0 && !maps;
+        // one pass written straight from registers into the destination: a frame, or the
+        // cropped output when its rows are 16-byte aligned 4-vectors (W % 4 == 0, r % 4 == 0)
+        const size_t oes = st == Storage::F32 ? 4 : 2;
+        const bool out_ok = !p.dst_is_output ||
+                            (st == Storage::F32 && W % 4 == 0 && ((uintptr_t)out % 16) == 0 && r % 4 == 0) ||
+                            (st != Storage::F32 && W % 4 == 0 && ((uintptr_t)out % 8) == 0 && r % 4 == 0);
+        (void)oes;
+        const bool direct = Dg == 1 && L.EX == r && tie == 0 && !maps && out_ok;
         int occ = occupancy_v2(st, r, tie != 0, maps != nullptr, direct, Dg);
         if (occ < 1) occ = 1;
         const long long g = (long long)occ * ctx->sms;

@@ -125,6 +125,7 @@ __device__ void process(const Job &jb, int g, int tile, unsigned char *smem) {
         gm.FH = jb.FH;
         gm.FW = jb.FW;
         gm.iy0 = gm.iy1 = gm.ix0 = gm.ix1 = 0;
+        gm.oy = gm.ox = gm.ly = gm.lx = 0;
         v2::pass_h2<R, float, false, false, false>(Uin, puin, R, A, L.P2, Uout, L.PU, nullptr, 0, gm, nullptr);
         __syncthreads();
         if (j < D && !interior) {

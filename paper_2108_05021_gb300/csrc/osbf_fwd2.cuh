@@ -236,6 +236,7 @@ struct Geom2 {
     int RHo, RWo;
     int fy0, fx0, FH, FW;
     int iy0, iy1, ix0, ix1;
+    int oy, ox, ly, lx;  // DIRECT destination: frame offset of its origin and its extent
 };
 
 template <int R, bool TIE_APP, bool IDX>
@@ -287,8 +288,11 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const float4 *urow = reinterpret_cast<const float4 *>(Uin + (yr + urow0) * pu_in + xs);
         float4 *orow = reinterpret_cast<float4 *>(Uout + yr * pu_out + xs);
         const int fy = g.fy0 + yo;
-        const bool row_store = DIRECT ? (row_ok && (unsigned)fy < (unsigned)g.FH) : row_ok;
-        T *grow = DIRECT ? gdst + (long long)(row_store ? fy : 0) * gpitch + g.fx0 + xs : nullptr;
+        // DIRECT: frame row fy lands in row fy - g.oy of the destination (0 for a frame,
+        // r for the cropped output), which has g.ly rows and g.lx columns
+        const int dy = fy - g.oy;
+        const bool row_store = DIRECT ? (row_ok && (unsigned)dy < (unsigned)g.ly) : row_ok;
+        T *grow = DIRECT ? gdst + (long long)(row_store ? dy : 0) * gpitch + (g.fx0 - g.ox) + xs : nullptr;
         const bool row_map = MAPS && row_ok && (unsigned)fy < (unsigned)g.FH && yo >= g.iy0 && yo < g.iy1;
         float ra[P], rb[P], ru[P], h6[P];  // raw a, b, U; and N6 sums (N5 at x is N6 at x - r)
         float2 hab[P];
@@ -371,7 +375,8 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 if (((t - 2 * R) & 3) == 3) {
                     const float4 v = make_float4(o[0], o[1], o[2], o[3]);
                     if (DIRECT) {
-                        if (row_store && g.fx0 + xo - 3 < g.FW) cvt_store4<T>(grow + (t - 2 * R - 3), v);
+                        const int dx = g.fx0 - g.ox + xo - 3;  // first column of the 4-vector
+                        if (row_store && (unsigned)dx < (unsigned)g.lx) cvt_store4<T>(grow + (t - 2 * R - 3), v);
                     } else if (row_ok) {
                         orow[(t - 2 * R) >> 2] = v;
                     }
@@ -501,6 +506,10 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(c
             g.iy1 = g.iy0 + TH;
             g.ix0 = L.EX - j * R;
             g.ix1 = g.ix0 + TW;
+            g.oy = p.dst_is_output ? R : 0;  // DIRECT into the cropped output needs W % 4 == 0
+            g.ox = g.oy;
+            g.ly = p.dst_is_output ? p.H : p.FH;
+            g.lx = p.dst_is_output ? p.W : p.FW;
             uint8_t *mplane = nullptr;
             if (MAPS && p.maps)
                 mplane =
