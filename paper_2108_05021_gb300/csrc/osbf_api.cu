@@ -276,9 +276,18 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     while (passes < iters) {
         const int Dg = iters - passes < D ? iters - passes : D;
         const bool last = passes + Dg == iters;
-        const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg)
-                              : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg)
-                                                   : v2::make_layout2<__nv_bfloat16>(r, Dg);
+        // one pass written straight from registers into the destination: a frame, or the
+        // cropped output when its rows hold 16-byte aligned 4-vectors (W % 4 == 0, r % 4 == 0).
+        // float32 frames: any r (the tile grid shifts so the halo stays exactly r columns);
+        // 16-bit frames: r % 8 == 0 (a 16-byte aligned halo)
+        const bool last_out = passes + Dg == iters && !out_is_frame;
+        const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
+                                          ((uintptr_t)out % (st == Storage::F32 ? 16 : 8)) == 0);
+        const bool direct = Dg == 1 && tie == 0 && !maps && out_ok && (st == Storage::F32 || r % 8 == 0);
+        const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
+                              : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
+                                                   : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
+        const int shift = (direct && st == Storage::F32) ? (4 - r % 4) % 4 : 0;
         CUtensorMap map;
         if (!encode_frame_map(&map, st, src, FW, FH, P, src_pitch, L.BX, L.RH0))
             return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame %dx%dx%d, pitch %d)", FW, FH, P,
@@ -313,28 +322,22 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
             p.dst_plane = (long long)FH * FWp;
             p.dst_pitch = FWp;
         }
-        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1) / v2::TW;
+        // tile k spans frame columns [k*TW - shift, (k+1)*TW - shift)
+        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1 + shift) / v2::TW;
         if (p.dst_is_output && !maps) {  // with maps, every frame pixel's selection is recorded
             ty0 = r / v2::TH;
             ty1 = (r + H - 1) / v2::TH;
-            tx0 = r / v2::TW;
-            tx1 = (r + W - 1) / v2::TW;
+            tx0 = (r + shift) / v2::TW;
+            tx1 = (r + W - 1 + shift) / v2::TW;
         }
         p.ty_off = ty0;
         p.tx_off = tx0;
+        p.tx_shift = shift;
         p.tiles_x = tx1 - tx0 + 1;
         p.tiles_y = ty1 - ty0 + 1;
         const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
         if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
         p.ntiles = (int)ntiles;
-        // one pass written straight from registers into the destination: a frame, or the
-        // cropped output when its rows are 16-byte aligned 4-vectors (W % 4 == 0, r % 4 == 0)
-        const size_t oes = st == Storage::F32 ? 4 : 2;
-        const bool out_ok = !p.dst_is_output ||
-                            (st == Storage::F32 && W % 4 == 0 && ((uintptr_t)out % 16) == 0 && r % 4 == 0) ||
-                            (st != Storage::F32 && W % 4 == 0 && ((uintptr_t)out % 8) == 0 && r % 4 == 0);
-        (void)oes;
-        const bool direct = Dg == 1 && L.EX == r && tie == 0 && !maps && out_ok;
         int occ = occupancy_v2(st, r, tie != 0, maps != nullptr, direct, Dg);
         if (occ < 1) occ = 1;
         const long long g = (long long)occ * ctx->sms;

@@ -50,7 +50,9 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     Layout2 L;
     const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
     L.EY = D * R;
-    L.EX = round_up(D * R, xa);
+    // direct float32 kernels keep the halo at exactly R columns; the tile grid is shifted
+    // by (4 - R % 4) % 4 columns instead, so the TMA box still starts on 16 bytes
+    L.EX = (direct && sizeof(T) == 4) ? D * R : round_up(D * R, xa);
     L.RH0 = TH + 2 * L.EY;
     L.RW0 = TW + 2 * L.EX;
     // pass H sweeps full SW-wide segments over the widest output region (RW0 - 2R): the
@@ -91,6 +93,7 @@ struct Fwd2Params {
     int D;
     int tiles_x, tiles_y, ntiles;  // tile grid; ntiles = tiles_x * tiles_y * planes
     int ty_off, tx_off;
+    int tx_shift;                  // tiles start at column k * TW - tx_shift (direct float32: (4 - R % 4) % 4)
     unsigned int *err;         // device error word (bit 0: a bounded wait gave up)
 };
 
@@ -271,6 +274,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                                         uint8_t *__restrict__ mplane) {
     constexpr int P = R + 1;         // ring period (the sweep is fully unrolled, so any period is static)
     constexpr int NS = SW + 2 * R;   // sweep steps of one segment (2R of warm-up)
+    constexpr int SH = (DIRECT && sizeof(T) == 4) ? (4 - R % 4) % 4 : 0;  // tile grid shift
     constexpr float iq = 1.0f / float((R + 1) * (R + 1));
     constexpr float ih = 1.0f / float((R + 1) * (2 * R + 1));
     const float2 iq2 = make_float2(iq, iq), ih2 = make_float2(ih, ih);
@@ -366,19 +370,26 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 int m;
                 select2<R, TIE_APP, MAPS>(d41, d32, d56, d87, ux, outv, m);
                 const int xo = xs + t - 2 * R;
-                o[(t - 2 * R) & 3] = storage_round<T>(outv);
+                // column of output o = t - 2R is congruent to o - SH mod 4 (SH: the grid shift)
+                o[(t - 2 * R - SH) & 3] = storage_round<T>(outv);
                 if (MAPS) {
                     const int fx = g.fx0 + xo;
                     if (row_map && (unsigned)fx < (unsigned)g.FW && xo >= g.ix0 && xo < g.ix1)
                         mplane[(long long)fy * g.FW + fx] = (uint8_t)m;
                 }
-                if (((t - 2 * R) & 3) == 3) {
+                const int oo = t - 2 * R;  // output index within the segment
+                if (DIRECT && SH > 0 && (oo < SH || oo >= SH + SW - 4)) {
+                    // the segment's first SH and last 4 - SH outputs share a 4-vector with a
+                    // neighbouring segment: store them one by one
+                    const int dx = g.fx0 - g.ox + xo;
+                    if (row_store && (unsigned)dx < (unsigned)g.lx) grow[oo] = from_f<T>(o[(oo - SH) & 3]);
+                } else if (((oo - SH) & 3) == 3) {
                     const float4 v = make_float4(o[0], o[1], o[2], o[3]);
                     if (DIRECT) {
                         const int dx = g.fx0 - g.ox + xo - 3;  // first column of the 4-vector
-                        if (row_store && (unsigned)dx < (unsigned)g.lx) cvt_store4<T>(grow + (t - 2 * R - 3), v);
+                        if (row_store && (unsigned)dx < (unsigned)g.lx) cvt_store4<T>(grow + (oo - 3), v);
                     } else if (row_ok) {
-                        orow[(t - 2 * R) >> 2] = v;
+                        orow[oo >> 2] = v;
                     }
                 }
             }
@@ -425,14 +436,14 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(c
 
     auto issue = [&](int tile) {
         const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
-        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
+        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
         tma_load_3d(smem_u32(bin), &src, tx0 - L.EX, ty0 - L.EY, plane, bar, (uint32_t)L.in_bytes);
     };
     // L2 prefetch of a tile's box: issued one tile ahead of its shared-memory load, so
     // that load is served from L2 instead of DRAM
     auto warm = [&](int tile) {
         const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
-        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
+        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
         tma_prefetch_l2_3d(&src, tx0 - L.EX, ty0 - L.EY, plane);
     };
     auto prefetch = [&](int tile) {
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(c
     uint32_t phase = 0;
     for (; tile < p.ntiles; tile += gridDim.x) {
         const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
-        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW;
+        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
         // wait for this tile's region (bounded: a copy that never lands is reported, not waited on forever)
         const bool timed_out = !mbar_wait_bounded(bar, phase);
         if (__syncthreads_or(timed_out)) {
