@@ -70,8 +70,10 @@ typedef struct {
     int depth;       /* passes fused per launch (temporal blocking), 1..OSBF_MAX_DEPTH;
                         0 = the tuned choice for (dtype, r, size) */
     int tie;         /* osbf_tie */
-    uint8_t *maps;   /* optional device buffer, iters x N*C x (H+2r) x (W+2r) bytes: the
-                        selected window index (1..8 = N1..N8) of every frame pixel and pass */
+    uint8_t *maps;   /* optional device buffer, iters x N*C x (H+2r) rows of
+                        osbf_maps_pitch(W, r) bytes, 16-byte aligned: the selected window
+                        index (1..8 = N1..N8) of every frame pixel and pass in the first
+                        W+2r bytes of each row (the rest of the row is unspecified) */
     int reserved[4]; /* must be zero */
 } osbf_options;
 
@@ -121,7 +123,8 @@ osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, in
  * window; the crop's transpose embeds the gradient into a zero frame and the
  * replicate pad's transpose folds the ring back onto the edge pixels.
  *   grad_out  N x C x H x W float32.      grad_in  N x C x H x W float32 (written).
- *   maps      iters x N*C x (H+2r) x (W+2r) uint8, as written by osbf_filter_ex().
+ *   maps      iters x N*C x (H+2r) rows of osbf_maps_pitch(W, r) uint8, as written by
+ *             osbf_filter_ex(); 16-byte aligned (else OSBF_EINVAL).
  */
 osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps,
                                  int N, int C, int H, int W, int r, int iters, void *stream);
@@ -129,6 +132,11 @@ osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *gr
 /* Row pitch, in float32 elements, of the padded frames the library stores
  * (checkpoints): (W + 2r) rounded up to a multiple of 32. */
 int osbf_frame_pitch(int W, int r);
+
+/* Row pitch, in bytes, of the selection maps: (W + 2r) rounded up to a multiple of 16
+ * (rows start on 16 bytes, so the maps can be written four selections at a time and
+ * read back by tensor copies). */
+int osbf_maps_pitch(int W, int r);
 
 /*
  * Checkpointed forward / backward (float32): instead of every pass's map, the

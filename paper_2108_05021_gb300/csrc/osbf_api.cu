@@ -188,6 +188,7 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     const int align_el = (int)(128 / fes);
     const int FWp = (FW + align_el - 1) / align_el * align_el;
     const size_t frame_bytes = fes * (size_t)P * FH * FWp;
+    const int MP = maps_pitch(FW);
 
     int D = depth > 0 ? depth : 0;
     if (D == 0) {
@@ -228,9 +229,10 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
             q.FW = FW;
             q.D = 1;
             q.maps = maps;
+            q.map_pitch = MP;
             q.map_iter0 = maps_iter0;
             q.map_iter_stride = maps_iter_stride;
-            q.map_plane = (long long)FH * FW;
+            q.map_plane = (long long)FH * MP;
             void *dst = direct ? out : (iters == 1 ? out : frame(0));
             if (!dst) return OSBF_ENOMEM;
             q.dst = dst;
@@ -283,7 +285,7 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         const bool last_out = passes + Dg == iters && !out_is_frame;
         const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
                                           ((uintptr_t)out % (st == Storage::F32 ? 16 : 8)) == 0);
-        const bool direct = Dg == 1 && tie == 0 && !maps && out_ok && (st == Storage::F32 || r % 8 == 0);
+        const bool direct = Dg == 1 && tie == 0 && out_ok && (st == Storage::F32 || r % 8 == 0);
         const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
                               : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
                                                    : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
@@ -300,9 +302,10 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         p.FW = FW;
         p.D = Dg;
         p.maps = maps;
+        p.map_pitch = MP;
         p.map_iter0 = maps_iter0 + passes;
         p.map_iter_stride = maps_iter_stride;
-        p.map_plane = (long long)FH * FW;
+        p.map_plane = (long long)FH * MP;
         p.err = ctx->err_word;
         int nxt = -1;
         if (last && !out_is_frame) {
@@ -452,7 +455,8 @@ osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int 
     const size_t out_bytes = (dtype == OSBF_U8 ? 4 : elem_size(dtype)) * (size_t)P * H * W;
     if (overlaps(in, in_bytes, out, out_bytes)) return fail(ctx, OSBF_EINVAL, "in and out overlap");
     const int FH = H + 2 * r, FW = W + 2 * r;
-    const long long map_stride = P * FH * FW;
+    const long long map_stride = P * FH * maps_pitch(FW);
+    if (o.maps && ((uintptr_t)o.maps & 15)) return fail(ctx, OSBF_EINVAL, "maps must be 16-byte aligned");
     if (o.maps && iters > 0 && (overlaps(o.maps, (size_t)map_stride * iters, in, in_bytes) ||
                                 overlaps(o.maps, (size_t)map_stride * iters, out, out_bytes)))
         return fail(ctx, OSBF_EINVAL, "maps overlap an image");
@@ -574,6 +578,7 @@ osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *gr
     ctx->err.clear();
     ctx->last_launches = 0;
     if (!grad_out || !grad_in || (!maps && iters > 0 && r > 0)) return fail(ctx, OSBF_EINVAL, "null pointer");
+    if (maps && ((uintptr_t)maps & 15)) return fail(ctx, OSBF_EINVAL, "maps must be 16-byte aligned");
     if (N <= 0 || C <= 0 || H <= 0 || W <= 0) return fail(ctx, OSBF_EINVAL, "N, C, H and W must be positive");
     if (r < 0 || iters < 0) return fail(ctx, OSBF_EINVAL, "r and iters must be >= 0");
     if (r > OSBF_MAX_RADIUS) return fail(ctx, OSBF_EUNSUPPORTED, "r exceeds OSBF_MAX_RADIUS");

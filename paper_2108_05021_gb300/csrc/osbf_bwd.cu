@@ -1,5 +1,6 @@
-// Backward of the One-Sided Box Filter: per-pass adjoint launches (osbf_bwd.cuh), the
-// transpose of the appendix's replicate padding, and the checkpointed forward/backward.
+// Backward of the One-Sided Box Filter: the transpose of the crop (embed into a zero
+// ring), per-pass adjoint launches (osbf_bwd.cuh), the transpose of the appendix's
+// replicate padding, and the checkpointed forward/backward.
 #include <cstring>
 
 #include "osbf.h"
@@ -16,14 +17,39 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
 
 namespace osbf {
 
-static cudaError_t launch_bwd(int R, const bwd::BwdParams &p, dim3 grid, cudaStream_t s) {
+static cudaError_t launch_bwd(int R, const CUtensorMap &gmap, const CUtensorMap &mmap, const bwd::BwdParams &p,
+                              int grid, cudaStream_t s) {
     switch (R) {
 #define OSBF_CASE(RR) \
-    case RR: return bwd::launch_bwd_tile<RR>(p, grid, s);
+    case RR: return bwd::launch_bwd_kernel<RR>(gmap, mmap, p, grid, s);
         OSBF_FOR_EACH_R(OSBF_CASE)
 #undef OSBF_CASE
     }
     return cudaErrorInvalidValue;
+}
+
+static int occupancy_bwd(int R) {
+    switch (R) {
+#define OSBF_CASE(RR) \
+    case RR: return bwd::occupancy_bwd_kernel<RR>();
+        OSBF_FOR_EACH_R(OSBF_CASE)
+#undef OSBF_CASE
+    }
+    return 0;
+}
+
+// Transpose of the crop: grad_out (H x W) inside the frame, zero on the ring.
+__global__ void embed_zero_kernel(const float *__restrict__ g, float *__restrict__ frame, int H, int W, int R, int FW,
+                                  int FWp) {
+    const int fy = blockIdx.y, plane = blockIdx.z;
+    const int y = fy - R;
+    const bool yin = (unsigned)y < (unsigned)H;
+    const float *src = g + ((long long)plane * H + (yin ? y : 0)) * W;
+    float *dst = frame + ((long long)plane * gridDim.y + fy) * FWp;
+    for (int fx = blockIdx.x * blockDim.x + threadIdx.x; fx < FW; fx += gridDim.x * blockDim.x) {
+        const int x = fx - R;
+        dst[fx] = (yin && (unsigned)x < (unsigned)W) ? src[x] : 0.f;
+    }
 }
 
 // Transpose of the replicate padding: each image pixel collects the gradient of every
@@ -47,53 +73,62 @@ __global__ void pad_adjoint_kernel(const float *__restrict__ g, float *__restric
 
 using namespace osbf;
 
+unsigned int *osbf_ctx_err_word(osbf_ctx *ctx);
+int osbf_ctx_sms(const osbf_ctx *ctx);
+
 namespace {
 
 int frame_pitch_f32(int FW) { return (FW + 31) / 32 * 32; }
 
 // The backward passes t = t1-1 .. t0 (maps + t * stride), starting from `g` (the caller's
-// grad_out when g_is_output, else a gradient frame); the result lands in one of two
-// gradient frames, returned through *result.
+// grad_out when g_is_output, else the gradient frame gbuf[*cur]); the result lands in one
+// of the two gradient frames, whose index is returned through *cur.
 osbf_status run_adjoint_passes(osbf_ctx *ctx, const float *g, int g_is_output, const uint8_t *maps, int t0, int t1,
                                int P, int H, int W, int r, float *gbuf[2], int *cur, cudaStream_t s) {
-    const int FH = H + 2 * r, FW = W + 2 * r, FWp = frame_pitch_f32(FW);
-    const long long mstride = (long long)P * FH * FW;
-    for (int t = t1 - 1; t >= t0; --t) {
-        bwd::BwdParams p;
-        std::memset(&p, 0, sizeof p);
-        if (g_is_output) {
-            p.gsrc = g;
-            p.src_is_output = 1;
-            p.src_plane = (long long)H * W;
-            p.src_pitch = W;
-        } else {
-            p.gsrc = gbuf[*cur];
-            p.src_plane = (long long)FH * FWp;
-            p.src_pitch = FWp;
-        }
-        const int nxt = g_is_output ? 0 : 1 - *cur;
-        p.gdst = gbuf[nxt];
-        p.dst_plane = (long long)FH * FWp;
-        p.dst_pitch = FWp;
-        p.maps = maps + (long long)t * mstride;
-        p.H = H;
-        p.W = W;
-        p.FH = FH;
-        p.FW = FW;
-        p.R = r;
+    const int FH = H + 2 * r, FW = W + 2 * r, FWp = frame_pitch_f32(FW), MP = maps_pitch(FW);
+    const long long mstride = (long long)P * FH * MP;
+    if (g_is_output) {
         for (int p0 = 0; p0 < P; p0 += 65535) {
             const int np = P - p0 < 65535 ? P - p0 : 65535;
-            bwd::BwdParams q = p;
-            q.gsrc = p.gsrc + (size_t)p0 * p.src_plane;
-            q.gdst = p.gdst + (size_t)p0 * p.dst_plane;
-            q.maps = p.maps + (size_t)p0 * FH * FW;
-            dim3 grid((FW + bwd::TW - 1) / bwd::TW, (FH + bwd::TH - 1) / bwd::TH, np);
-            cudaError_t e = launch_bwd(r, q, grid, s);
+            dim3 grid((FW + 255) / 256 < 8 ? (FW + 255) / 256 : 8, FH, np);
+            embed_zero_kernel<<<grid, 256, 0, s>>>(g + (size_t)p0 * H * W, gbuf[0] + (size_t)p0 * FH * FWp, H, W, r,
+                                                   FW, FWp);
+            cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return osbf_ctx_fail(ctx, OSBF_ECUDA, cudaGetErrorString(e));
             osbf_ctx_count_launches(ctx, 1);
         }
+        *cur = 0;
+    }
+    const bwd::BLayout L = bwd::make_blayout(r);
+    int occ = occupancy_bwd(r);
+    if (occ < 1) occ = 1;
+    const int shift = (16 - r % 16) % 16;  // tile k starts at column k * TW - shift: boxes start on 16 bytes
+    bwd::BwdParams p;
+    std::memset(&p, 0, sizeof p);
+    p.dst_plane = (long long)FH * FWp;
+    p.dst_pitch = FWp;
+    p.FH = FH;
+    p.FW = FW;
+    p.tiles_x = (FW - 1 + shift) / bwd::TW + 1;
+    p.tiles_y = (FH + bwd::TH - 1) / bwd::TH;
+    const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
+    if (ntiles > 0x7fffffffLL) return osbf_ctx_fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
+    p.ntiles = (int)ntiles;
+    p.tx_shift = shift;
+    p.err = osbf_ctx_err_word(ctx);
+    const long long gmax = (long long)occ * osbf_ctx_sms(ctx);
+    const int grid = (int)(gmax < ntiles ? gmax : ntiles);
+    for (int t = t1 - 1; t >= t0; --t) {
+        CUtensorMap gmap, mmap;
+        if (!encode_frame_map(&gmap, Storage::F32, gbuf[*cur], FW, FH, P, FWp, L.BXg, L.RH) ||
+            !encode_frame_map(&mmap, Storage::U8, maps + t * mstride, FW, FH, P, MP, L.BXm, L.RH))
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (backward)");
+        const int nxt = 1 - *cur;
+        p.gdst = gbuf[nxt];
+        cudaError_t e = launch_bwd(r, gmap, mmap, p, grid, s);
+        if (e != cudaSuccess) return osbf_ctx_fail(ctx, OSBF_ECUDA, cudaGetErrorString(e));
+        osbf_ctx_count_launches(ctx, 1);
         *cur = nxt;
-        g_is_output = 0;
     }
     return OSBF_OK;
 }
@@ -133,6 +168,8 @@ osbf_status osbf_backward_impl(osbf_ctx *ctx, const float *grad_out, float *grad
 extern "C" {
 
 int osbf_frame_pitch(int W, int r) { return frame_pitch_f32(W + 2 * r); }
+
+int osbf_maps_pitch(int W, int r) { return maps_pitch(W + 2 * r); }
 
 osbf_status osbf_filter_checkpointed(osbf_ctx *ctx, const float *in, float *out, float *checkpoints, int interval,
                                      int N, int C, int H, int W, int r, int iters, void *stream) {
@@ -189,7 +226,7 @@ osbf_status osbf_filter_backward_checkpointed(osbf_ctx *ctx, const float *grad_o
         return OSBF_OK;
     }
     const long long fstride = (long long)P * FH * FWp;
-    const long long mstride = (long long)P * FH * FW;
+    const long long mstride = (long long)P * FH * maps_pitch(FW);
     const int K = (iters + interval - 1) / interval;
     osbf_status st;
     const size_t fb = sizeof(float) * (size_t)fstride;

@@ -1,4 +1,4 @@
-// osbf_bwd.cuh -- adjoint (backward) tile kernel of the One-Sided Box Filter (sm_103a).
+// osbf_bwd.cuh -- adjoint (backward) kernel of the One-Sided Box Filter (sm_103a).
 //
 // With every pixel's selection m(p) frozen, one pass of Algorithm 2 is linear:
 //   U'(p) = (1/n_m(p)) * sum_{o in O_m(p)} U(p + o)       (zero outside the padded frame),
@@ -13,52 +13,68 @@
 //   F3(y) = Vup(c5)(y) + Vup(c6)(y + r)               c5 = G_7,              c6 = G_8
 // (mirrored N2 / N3 / N6 / N7 / N8 evaluate HL at x, mirrored N1 / N4 / N5 / N7 / N8 at
 // x + r; the full-width rows of N7 / N8 subtract their centre column once).
-// One CTA owns a 32 x 128 tile: pass V sweeps columns computing the six column sums,
-// pass H sweeps row segments computing the two left sums -- the same O(1)-in-r
-// structure as the forward.  One launch per pass (the forward's maps of that pass).
+//
+// Organisation (persistent and TMA-fed, like the forward kernel):
+//   * each CTA walks the tile list; a tile's region of the incoming gradient frame
+//     (float32) and of the pass's selection map (uint8) arrive by two TMA tensor loads
+//     on one mbarrier; out-of-frame elements read 0 (zero gradient; window 0 = none);
+//   * pass V (one thread per region column) keeps the six column sums as three packed
+//     f32x2 running sums over a register ring, and emits F1, F2 into a float2 field and
+//     F3 in place over the gradient box (a thread overwrites only rows of its own column
+//     that it has already consumed);
+//   * pass H (one lane per tile row) keeps the two left row sums as one f32x2 and writes
+//     g_in from registers into the outgoing gradient frame, four columns per 16-byte store;
+//   * the tile grid is shifted by (16 - r % 16) % 16 columns, so both boxes start on
+//     16 bytes (the TMA rule), and the stores are realigned in-lane.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "osbf_fwd2.cuh"
 
 namespace osbf {
 namespace bwd {
 
-constexpr int TH = 32, TW = 128, SW = 32, NT = 128;
+constexpr int TH = 32, TW = 128, SW = 32;
+constexpr int NT = 160;  // one thread per region column (TW + 2r <= 160 for r <= 16)
 
 struct BwdParams {
-    const float *gsrc;       // incoming gradient: a padded frame, or the caller's grad_out (src_is_output)
-    int src_is_output;       // 1: gsrc is H x W (embed into a zero frame); 0: frame with pitch src_pitch
-    long long src_plane;
-    int src_pitch;
-    const uint8_t *maps;     // this pass's selections, P x FH x FW
-    float *gdst;             // outgoing gradient frame (pitch dst_pitch)
-    long long dst_plane;
+    float *gdst;          // outgoing gradient frame (pitch dst_pitch floats)
+    long long dst_plane;  // floats per plane of gdst
     int dst_pitch;
-    int H, W, FH, FW, R;
+    int FH, FW;
+    int tiles_x, tiles_y, ntiles;
+    int tx_shift;         // tile k starts at frame column k * TW - tx_shift
+    unsigned int *err;    // device error word (bit 0: a bounded wait gave up)
 };
 
 struct BLayout {
-    int RH, RW, PG, PF;  // region rows / cols; float pitch of the g box; float2 pitch of the (F1, F2) field
-    int off_g, off_m, off_f12, off_f3, bytes;
+    int RH, RW;  // region rows / columns
+    int BXg;     // gradient box width (floats): >= RW + 3 (pass H's float4 over-read), BXg / 4 odd
+    int BXm;     // selection box width (bytes): >= RW, a multiple of 16
+    int PF;      // float2 row pitch of the (F1, F2) field: >= RW, PF % 4 == 2
+    int off_g, off_m, off_f, bytes;
 };
 
 __host__ __device__ inline BLayout make_blayout(int R) {
     BLayout L;
     L.RH = TH + 2 * R;
     L.RW = TW + 2 * R;
-    L.PG = L.RW + 9;  // odd: lanes = rows read F3 conflict-free
-    if ((L.PG & 1) == 0) ++L.PG;
-    L.PF = L.PG;      // odd float2 pitch: conflict-free 8-byte row-owner loads
+    L.BXg = (L.RW + 3 + 3) / 4 * 4;
+    if (((L.BXg / 4) & 1) == 0) L.BXg += 4;  // odd float4 pitch: conflict-free row-owner loads
+    L.BXm = (L.RW + 15) / 16 * 16;
+    L.PF = L.RW;
+    while (L.PF % 4 != 2) ++L.PF;            // odd float4 pitch
     L.off_g = 0;
-    L.off_m = L.off_g + L.RH * L.PG * 4;
-    L.off_f12 = (L.off_m + L.RH * L.PG + 15) & ~15;
-    L.off_f3 = L.off_f12 + TH * L.PF * 8;
-    L.bytes = L.off_f3 + TH * L.PG * 4 + 64;
+    L.off_m = v2::align128(L.RH * L.BXg * 4);
+    L.off_f = v2::align128(L.off_m + L.RH * L.BXm);
+    L.bytes = L.off_f + TH * L.PF * 8 + 16;  // + mbarrier
     return L;
 }
 
-// which column-sum inputs c1..c6 receive G_m (bit j-1 for c_j), and whether it is G_5 / G_6
+// which column-sum inputs c1..c6 receive G_m (bit j-1 for c_j)
 __device__ __forceinline__ unsigned cmask(int m) {
     // m:      1        2        3        4        5         6         7          8
     // c-bits: c3       c1       c2       c4       c3,c4     c1,c2     c1,c3,c5   c2,c4,c6
@@ -67,167 +83,230 @@ __device__ __forceinline__ unsigned cmask(int m) {
     return m == 8 ? 0x2Au : (unsigned)(lut >> (8 * m)) & 0xFFu;
 }
 
+// pass V: thread = region column c.  Writes F1, F2 of tile rows y in [0, TH) to F12 and
+// F3 over the gradient box's row y.
 template <int R>
-__global__ void __launch_bounds__(NT, 2) osbf_bwd_tile(const BwdParams p) {
-    extern __shared__ __align__(16) unsigned char bsm[];
-    const BLayout L = make_blayout(R);
-    float *gb = reinterpret_cast<float *>(bsm + L.off_g);
-    uint8_t *mb = bsm + L.off_m;
-    float2 *F12 = reinterpret_cast<float2 *>(bsm + L.off_f12);
-    float *F3 = reinterpret_cast<float *>(bsm + L.off_f3);
+__device__ __forceinline__ void bwd_pass_v(float *__restrict__ gb, const uint8_t *__restrict__ mb,
+                                           float2 *__restrict__ F12, const BLayout &L) {
+    constexpr int P = R + 1;
+    constexpr int RH = TH + 2 * R;
     constexpr float iq = 1.0f / float((R + 1) * (R + 1));
     constexpr float ih = 1.0f / float((R + 1) * (2 * R + 1));
+    const int c = threadIdx.x;
+    if (c >= L.RW) return;
+    float *gcol = gb + c;
+    const uint8_t *mcol = mb + c;
+    float2 r12[P], r34[P], r56[P];  // (c1, c2), (c3, c4), (c5, c6) of the last P rows
+    float2 q13[P];                  // (V1 - G6, V3 - G5) at each of the last P rows
+    float q5[P];                    // V5 at each of the last P rows
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        r12[k] = make_float2(0.f, 0.f);
+        r34[k] = r12[k];
+        r56[k] = r12[k];
+    }
+    float2 V12 = make_float2(0.f, 0.f), V34 = V12, V56 = V12;
+#pragma unroll
+    for (int s = 0; s < RH; ++s) {
+        const int k = s % P;
+        const float gv = gcol[s * L.BXg];
+        const int m = mcol[s * L.BXm];
+        const float w = gv * (m <= 4 ? iq : ih);
+        const unsigned cm = cmask(m);
+        const float2 n12 = make_float2((cm & 1u) ? w : 0.f, (cm & 2u) ? w : 0.f);
+        const float2 n34 = make_float2((cm & 4u) ? w : 0.f, (cm & 8u) ? w : 0.f);
+        const float2 n56 = make_float2((cm & 16u) ? w : 0.f, (cm & 32u) ? w : 0.f);
+        if (k == P - 1) {  // the ring holds the whole window: re-form the sums (bounded FP32 drift)
+            r12[k] = n12;
+            r34[k] = n34;
+            r56[k] = n56;
+            V12 = r12[0];
+            V34 = r34[0];
+            V56 = r56[0];
+#pragma unroll
+            for (int i = 1; i < P; ++i) {
+                V12 = v2::add2(V12, r12[i]);
+                V34 = v2::add2(V34, r34[i]);
+                V56 = v2::add2(V56, r56[i]);
+            }
+        } else {  // slot k holds row s - R - 1 (zeros before the window fills)
+            V12 = v2::add2(V12, v2::sub2(n12, r12[k]));
+            V34 = v2::add2(V34, v2::sub2(n34, r34[k]));
+            V56 = v2::add2(V56, v2::sub2(n56, r56[k]));
+            r12[k] = n12;
+            r34[k] = n34;
+            r56[k] = n56;
+        }
+        // the parts of F1 / F2 / F3 that belong to row s as the upper window's bottom row
+        q13[k] = make_float2(V12.x - (m == 6 ? w : 0.f), V34.x - (m == 5 ? w : 0.f));
+        q5[k] = V56.x;
+        if (s >= 2 * R) {
+            const int y = s - 2 * R;
+            const int sl = (s - R) % P;  // row s - R = y + R (frame row y of the formula)
+            F12[y * L.PF + c] = make_float2(q13[sl].x + V12.y, q13[sl].y + V34.y);
+            gcol[y * L.BXg] = q5[sl] + V56.y;  // row y of this column was consumed at step y
+        }
+    }
+}
 
-    const int plane = blockIdx.z;
-    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-    const int fy0 = ty0 - R, fx0 = tx0 - R;  // frame coordinates of the region origin
+// pass H: lane = tile row, warp = one SW-column segment.  g_in of the tile goes from
+// registers to the outgoing frame; SH realigns the 4-vectors to 16-byte columns.
+template <int R>
+__device__ __forceinline__ void bwd_pass_h(const float *__restrict__ gb, const float2 *__restrict__ F12,
+                                           const BLayout &L, float *__restrict__ gdst, int pitch, int ty0, int tx0,
+                                           int FH, int FW) {
+    constexpr int P = R + 1;
+    constexpr int NS = SW + 2 * R;
+    constexpr int SH = (4 - R % 4) % 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // ---- load g and the selections of the region (zero outside the frame) ----
-    const float *gsrc = p.gsrc + (long long)plane * p.src_plane;
-    const uint8_t *msrc = p.maps + (long long)plane * p.FH * p.FW;
-    for (int y = warp; y < L.RH; y += NT / 32) {
-        const int fy = fy0 + y;
-        const bool yin = (unsigned)fy < (unsigned)p.FH;
-        for (int x = lane; x < L.RW; x += 32) {
-            const int fx = fx0 + x;
-            float g = 0.f;
-            int m = 0;
-            if (yin && (unsigned)fx < (unsigned)p.FW) {
-                m = msrc[(long long)fy * p.FW + fx];
-                if (p.src_is_output) {  // the crop's transpose: grad_out inside, zero on the ring
-                    const int oy = fy - p.R, ox = fx - p.R;
-                    if ((unsigned)oy < (unsigned)p.H && (unsigned)ox < (unsigned)p.W)
-                        g = gsrc[(long long)oy * p.src_pitch + ox];
-                } else {
-                    g = gsrc[(long long)fy * p.src_pitch + fx];
-                }
-            }
-            gb[y * L.PG + x] = g;
-            mb[y * L.PG + x] = (uint8_t)m;
+    if (warp >= TW / SW) return;
+    const int y = lane, xs = warp * SW;
+    const int fy = ty0 + y;
+    const bool row_store = (unsigned)fy < (unsigned)FH;
+    float *grow = gdst + (long long)(row_store ? fy : 0) * pitch + tx0 + xs;
+    const float4 *frow = reinterpret_cast<const float4 *>(F12 + y * L.PF + xs);
+    const float4 *f3row = reinterpret_cast<const float4 *>(gb + y * L.BXg + xs);
+    float2 r12[P];
+    float h1[P], r3[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) r12[k] = make_float2(0.f, 0.f);
+    float2 HL = make_float2(0.f, 0.f);
+    float4 v12 = make_float4(0.f, 0.f, 0.f, 0.f), v3 = v12;
+    float o[4];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const int k = t % P;
+        if ((t & 1) == 0) v12 = frow[t >> 1];
+        if ((t & 3) == 0) v3 = f3row[t >> 2];
+        const float2 f = (t & 1) ? make_float2(v12.z, v12.w) : make_float2(v12.x, v12.y);
+        r3[k] = f4get(v3, t & 3);
+        if (k == P - 1 || R <= 2) {
+            r12[k] = f;
+            HL = r12[0];
+#pragma unroll
+            for (int i = 1; i < P; ++i) HL = v2::add2(HL, r12[i]);
+        } else {  // slot k holds column t - R - 1 (zeros before the window fills)
+            HL = v2::add2(HL, v2::sub2(f, r12[k]));
+            r12[k] = f;
         }
-    }
-    __syncthreads();
-
-    // ---- pass V: per column, running up sums of c1..c6; F at output row y = s - 2R ----
-    for (int c = threadIdx.x; c < L.RW; c += NT) {
-        constexpr int P = R + 1;
-        float2 r12[P], r34[P], r56[P];  // c-pairs by row slot (leave the window R + 1 rows later)
-        float2 h13[P], h5e[P];          // (V1, V3)(s) and (V5, 0) by slot, plus (G5, G6) raw
-        float2 e56[P];
-        float2 V12 = make_float2(0.f, 0.f), V34 = V12, V56 = V12;
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-            r12[k] = make_float2(0.f, 0.f);
-            r34[k] = r12[k];
-            r56[k] = r12[k];
-        }
-        const int RH = L.RH;
-        for (int s0 = 0; s0 < RH; s0 += P) {
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const int s = s0 + k;
-                if (s < RH) {
-                    const int m = mb[s * L.PG + c];
-                    const float w = gb[s * L.PG + c] * (m <= 4 ? iq : ih);
-                    const unsigned cm = cmask(m);
-                    const float2 n12 = make_float2((cm & 1u) ? w : 0.f, (cm & 2u) ? w : 0.f);
-                    const float2 n34 = make_float2((cm & 4u) ? w : 0.f, (cm & 8u) ? w : 0.f);
-                    const float2 n56 = make_float2((cm & 16u) ? w : 0.f, (cm & 32u) ? w : 0.f);
-                    if (k == P - 1) {  // re-form the window sums from the ring (bounded FP32 drift)
-                        r12[k] = n12;
-                        r34[k] = n34;
-                        r56[k] = n56;
-                        V12 = r12[0];
-                        V34 = r34[0];
-                        V56 = r56[0];
-#pragma unroll
-                        for (int i = 1; i < P; ++i) {
-                            V12 = __fadd2_rn(V12, r12[i]);
-                            V34 = __fadd2_rn(V34, r34[i]);
-                            V56 = __fadd2_rn(V56, r56[i]);
-                        }
-                    } else {
-                        V12 = __fadd2_rn(V12, __fadd2_rn(n12, make_float2(-r12[k].x, -r12[k].y)));
-                        V34 = __fadd2_rn(V34, __fadd2_rn(n34, make_float2(-r34[k].x, -r34[k].y)));
-                        V56 = __fadd2_rn(V56, __fadd2_rn(n56, make_float2(-r56[k].x, -r56[k].y)));
-                        r12[k] = n12;
-                        r34[k] = n34;
-                        r56[k] = n56;
-                    }
-                    h13[k] = make_float2(V12.x, V34.x);  // (V1, V3) at row s
-                    h5e[k] = make_float2(V56.x, 0.f);    // V5 at row s
-                    e56[k] = make_float2(m == 5 ? w : 0.f, m == 6 ? w : 0.f);
-                    if (s >= 2 * R) {
-                        const int sl = (k + 1) % P;  // row s - R
-                        const int y = s - 2 * R;
-                        const float f1 = h13[sl].x + V12.y - e56[sl].y;  // V1(y+R) + V2(y+2R) - G6(y+R)
-                        const float f2 = h13[sl].y + V34.y - e56[sl].x;  // V3(y+R) + V4(y+2R) - G5(y+R)
-                        const float f3 = h5e[sl].x + V56.y;              // V5(y+R) + V6(y+2R)
-                        F12[y * L.PF + c] = make_float2(f1, f2);
-                        F3[y * L.PG + c] = f3;
-                    }
-                }
+        h1[k] = HL.x;
+        if (t >= 2 * R) {
+            const int sl = (t - R) % P;  // region column t - R: the output pixel's column
+            const int oo = t - 2 * R;    // output index within the segment
+            const int slot = (oo - SH) & 3;
+            o[slot] = h1[sl] + HL.y - r3[sl];
+            if (SH > 0 && (oo < SH || oo >= SH + SW - 4)) {
+                const int fx = tx0 + xs + oo;
+                if (row_store && (unsigned)fx < (unsigned)FW) grow[oo] = o[slot];
+            } else if (slot == 3) {
+                const int fx = tx0 + xs + oo - 3;  // first column of the 4-vector (16-byte aligned)
+                if (row_store && (unsigned)fx < (unsigned)FW)
+                    *reinterpret_cast<float4 *>(grow + oo - 3) = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
-    }
-    __syncthreads();
-
-    // ---- pass H: g_in(y, x) = HL[F1](x) + HL[F2](x + R) - F3(x), x in [R, R + TW) ----
-    float *gdst = p.gdst + (long long)plane * p.dst_plane;
-    for (int item = warp; item < TW / SW; item += NT / 32) {
-        const int y = lane;  // output row (TH == 32)
-        const int xs = item * SW;
-        constexpr int P = R + 1;
-        constexpr int NS = SW + 2 * R;
-        float2 r12[P], h12[P];
-        float r3[P];
-        float2 HL = make_float2(0.f, 0.f);
-        const float2 *frow = F12 + y * L.PF + xs;
-        const float *f3row = F3 + y * L.PG + xs;
-        float *orow = gb + y * L.PG;  // the g box is dead after pass V: stage the tile there
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-            const int k = t % P;
-            const float2 f = frow[t];
-            r3[k] = f3row[t];
-            if (t < R) {
-                r12[k] = f;
-                continue;
-            }
-            if (k == P - 1 || t == R || R <= 3) {
-                r12[k] = f;
-                HL = f;
-#pragma unroll
-                for (int i = 1; i <= R; ++i) HL = __fadd2_rn(HL, r12[(k + P - i) % P]);
-            } else {  // slot k holds the value leaving the window (R + 1 steps back)
-                HL = __fadd2_rn(HL, __fadd2_rn(f, make_float2(-r12[k].x, -r12[k].y)));
-                r12[k] = f;
-            }
-            h12[k] = HL;
-            if (t >= 2 * R) {
-                const int sl = (k + 1) % P;   // column x = t - R (region coordinates)
-                const int x = xs + t - 2 * R;  // tile column
-                orow[x] = h12[sl].x + HL.y - r3[sl];
-            }
-        }
-    }
-    __syncthreads();
-    // coalesced copy of the tile to the outgoing gradient frame
-    for (int i = threadIdx.x; i < TH * TW; i += NT) {
-        const int y = i / TW, x = i % TW;
-        const int fy = ty0 + y, fx = tx0 + x;
-        if (fy < p.FH && fx < p.FW) gdst[(long long)fy * p.dst_pitch + fx] = gb[y * L.PG + x];
     }
 }
 
 template <int R>
-cudaError_t launch_bwd_tile(const BwdParams &p, dim3 grid, cudaStream_t s) {
+__global__ void __launch_bounds__(NT, R <= 8 ? 3 : 2)
+    osbf_bwd_kernel(const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap mmap,
+                    const BwdParams p) {
+    extern __shared__ __align__(128) unsigned char bsm[];
     const BLayout L = make_blayout(R);
-    cudaError_t e = cudaFuncSetAttribute(osbf_bwd_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
+    float *gb = reinterpret_cast<float *>(bsm + L.off_g);
+    uint8_t *mb = bsm + L.off_m;
+    float2 *F12 = reinterpret_cast<float2 *>(bsm + L.off_f);
+    const uint32_t bar = v2::smem_u32(bsm + L.bytes - 16);
+    const uint32_t box_bytes = (uint32_t)(L.RH * L.BXg * 4 + L.RH * L.BXm);
+    const int tiles_per_plane = p.tiles_x * p.tiles_y;
+
+    if (threadIdx.x == 0) {
+        v2::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        v2::fence_proxy_async();
+    }
+    __syncthreads();
+
+    auto origin = [&](int tile, int &plane, int &ty0, int &tx0) {
+        plane = tile / tiles_per_plane;
+        const int rem = tile % tiles_per_plane;
+        ty0 = (rem / p.tiles_x) * TH;
+        tx0 = (rem % p.tiles_x) * TW - p.tx_shift;
+    };
+    auto issue = [&](int tile) {
+        int plane, ty0, tx0;
+        origin(tile, plane, ty0, tx0);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(box_bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(v2::smem_u32(gb)),
+            "l"(reinterpret_cast<uint64_t>(&gmap)), "r"(tx0 - R), "r"(ty0 - R), "r"(plane), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(v2::smem_u32(mb)),
+            "l"(reinterpret_cast<uint64_t>(&mmap)), "r"(tx0 - R), "r"(ty0 - R), "r"(plane), "r"(bar)
+            : "memory");
+    };
+    auto warm = [&](int tile) {  // L2 prefetch one tile ahead of its shared-memory load
+        int plane, ty0, tx0;
+        origin(tile, plane, ty0, tx0);
+        v2::tma_prefetch_l2_3d(&gmap, tx0 - R, ty0 - R, plane);
+        v2::tma_prefetch_l2_3d(&mmap, tx0 - R, ty0 - R, plane);
+    };
+
+    int tile = blockIdx.x;
+    if (tile < p.ntiles && threadIdx.x == 0) {
+        issue(tile);
+        if (tile + (int)gridDim.x < p.ntiles) warm(tile + gridDim.x);
+    }
+    uint32_t phase = 0;
+    for (; tile < p.ntiles; tile += gridDim.x) {
+        int plane, ty0, tx0;
+        origin(tile, plane, ty0, tx0);
+        const bool timed_out = !v2::mbar_wait_bounded(bar, phase);
+        if (__syncthreads_or(timed_out)) {
+            // report; thread 0 gives the copies one more bounded wait, so the CTA's shared
+            // memory outlives copies that are merely late
+            if (threadIdx.x == 0) {
+                atomicOr(p.err, 1u);
+                v2::mbar_wait_bounded(bar, phase);
+            }
+            return;
+        }
+        phase ^= 1;
+        bwd_pass_v<R>(gb, mb, F12, L);
+        __syncthreads();
+        bwd_pass_h<R>(gb, F12, L, p.gdst + (long long)plane * p.dst_plane, p.dst_pitch, ty0, tx0, p.FH, p.FW);
+        __syncthreads();
+        const int next = tile + gridDim.x;
+        if (next < p.ntiles && threadIdx.x == 0) {  // both boxes are dead: load the next tile
+            v2::fence_proxy_async();
+            issue(next);
+            if (next + (int)gridDim.x < p.ntiles) warm(next + gridDim.x);
+        }
+    }
+}
+
+template <int R>
+cudaError_t launch_bwd_kernel(const CUtensorMap &gmap, const CUtensorMap &mmap, const BwdParams &p, int grid,
+                              cudaStream_t s) {
+    const BLayout L = make_blayout(R);
+    cudaError_t e = cudaFuncSetAttribute(osbf_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
-    osbf_bwd_tile<R><<<grid, NT, L.bytes, s>>>(p);
+    osbf_bwd_kernel<R><<<grid, NT, L.bytes, s>>>(gmap, mmap, p);
     return cudaGetLastError();
+}
+
+template <int R>
+int occupancy_bwd_kernel() {
+    const BLayout L = make_blayout(R);
+    if (cudaFuncSetAttribute(osbf_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) !=
+        cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, osbf_bwd_kernel<R>, NT, L.bytes) != cudaSuccess) return 0;
+    return n;
 }
 
 }  // namespace bwd

@@ -70,7 +70,8 @@ __host__ __device__ inline Layout make_layout(int R, int D, int xalign) {
 struct FwdParams {
     const void *src;        // group input: the caller's image (src_is_input) or a padded frame
     void *dst;              // group output: a padded frame or the caller's output (dst_is_output)
-    uint8_t *maps;          // selection maps [iters][P][FH][FW] or null
+    uint8_t *maps;          // selection maps [iters][P][FH][map_pitch] or null
+    int map_pitch;          // bytes per map row
     long long src_plane, dst_plane;  // elements per plane
     int src_pitch, dst_pitch;        // elements per row
     int H, W, FH, FW;
@@ -254,6 +255,7 @@ struct PassHGeom {
     int fy0, fx0;       // frame coordinates of the U^j region origin
     int FH, FW;
     int iy0, iy1, ix0, ix1;  // tile interior in U^j region coordinates (map writes)
+    int MP;                  // map row pitch (bytes)
 };
 
 template <int R, typename TSt, bool TIE_APP, bool MAPS, bool U8X>
@@ -347,7 +349,7 @@ __device__ __forceinline__ void pass_h(const float *__restrict__ Uin, const floa
                         const int oi = (k - 2 * R) & 3;
                         o[oi] = outv;
                         if (MAPS) {
-                            if (row_map && in && xo >= g.ix0 && xo < g.ix1) mplane[(long long)fy * g.FW + fx] = (uint8_t)m;
+                            if (row_map && in && xo >= g.ix0 && xo < g.ix1) mplane[(long long)fy * g.MP + fx] = (uint8_t)m;
                         }
                         if (oi == 3 && row_ok)
                             *reinterpret_cast<float4 *>(orow + (t - 2 * R - 3)) = make_float4(o[0], o[1], o[2], o[3]);
@@ -393,6 +395,7 @@ __global__ void __launch_bounds__(kNT, 3) osbf_fwd_tile(const FwdParams p) {
         g.iy1 = g.iy0 + kTH;
         g.ix0 = L.EX - j * R;
         g.ix1 = g.ix0 + kTW;
+        g.MP = p.map_pitch;
         uint8_t *mplane = nullptr;
         if (MAPS && p.maps)
             mplane = p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;

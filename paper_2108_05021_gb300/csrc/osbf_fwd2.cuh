@@ -86,7 +86,8 @@ struct Fwd2Params {
     int dst_is_output;
     long long dst_plane;
     int dst_pitch;
-    uint8_t *maps;
+    uint8_t *maps;             // selection maps [iters][P][FH][map_pitch] or null
+    int map_pitch;             // bytes per map row (a multiple of 16)
     int map_iter0;
     long long map_iter_stride, map_plane;
     int H, W, FH, FW;
@@ -240,6 +241,7 @@ struct Geom2 {
     int fy0, fx0, FH, FW;
     int iy0, iy1, ix0, ix1;
     int oy, ox, ly, lx;  // DIRECT destination: frame offset of its origin and its extent
+    int MP;              // map row pitch (bytes)
 };
 
 template <int R, bool TIE_APP, bool IDX>
@@ -297,7 +299,8 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const int dy = fy - g.oy;
         const bool row_store = DIRECT ? (row_ok && (unsigned)dy < (unsigned)g.ly) : row_ok;
         T *grow = DIRECT ? gdst + (long long)(row_store ? dy : 0) * gpitch + (g.fx0 - g.ox) + xs : nullptr;
-        const bool row_map = MAPS && row_ok && (unsigned)fy < (unsigned)g.FH && yo >= g.iy0 && yo < g.iy1;
+        const bool row_map =
+            MAPS && mplane != nullptr && row_ok && (unsigned)fy < (unsigned)g.FH && yo >= g.iy0 && yo < g.iy1;
         float ra[P], rb[P], ru[P], h6[P];  // raw a, b, U; and N6 sums (N5 at x is N6 at x - r)
         float2 hab[P];
 #pragma unroll
@@ -310,6 +313,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         float UL = 0.f;
         float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va, vu = va;
         float o[4];
+        uint32_t mw = 0;  // DIRECT maps: selections of the current 4-column group
         // the whole segment is unrolled: ring slots, loads, warm-up and stores are static
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
@@ -370,24 +374,38 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 int m;
                 select2<R, TIE_APP, MAPS>(d41, d32, d56, d87, ux, outv, m);
                 const int xo = xs + t - 2 * R;
-                // column of output o = t - 2R is congruent to o - SH mod 4 (SH: the grid shift)
-                o[(t - 2 * R - SH) & 3] = storage_round<T>(outv);
-                if (MAPS) {
+                const int oo = t - 2 * R;  // output index within the segment
+                // column of output oo is congruent to oo - SH mod 4 (SH: the grid shift)
+                const int slot = (oo - SH) & 3;
+                o[slot] = storage_round<T>(outv);
+                if (MAPS && DIRECT) {  // four selections per 32-bit word, like the outputs
+                    mw = slot == 0 ? (uint32_t)m : mw | ((uint32_t)m << (8 * slot));
+                } else if (MAPS) {
                     const int fx = g.fx0 + xo;
                     if (row_map && (unsigned)fx < (unsigned)g.FW && xo >= g.ix0 && xo < g.ix1)
-                        mplane[(long long)fy * g.FW + fx] = (uint8_t)m;
+                        mplane[(long long)fy * g.MP + fx] = (uint8_t)m;
                 }
-                const int oo = t - 2 * R;  // output index within the segment
                 if (DIRECT && SH > 0 && (oo < SH || oo >= SH + SW - 4)) {
                     // the segment's first SH and last 4 - SH outputs share a 4-vector with a
                     // neighbouring segment: store them one by one
                     const int dx = g.fx0 - g.ox + xo;
-                    if (row_store && (unsigned)dx < (unsigned)g.lx) grow[oo] = from_f<T>(o[(oo - SH) & 3]);
-                } else if (((oo - SH) & 3) == 3) {
+                    if (row_store && (unsigned)dx < (unsigned)g.lx) grow[oo] = from_f<T>(o[slot]);
+                    if (MAPS) {
+                        const int fx = g.fx0 + xo;
+                        if (row_map && (unsigned)fx < (unsigned)g.FW) mplane[(long long)fy * g.MP + fx] = (uint8_t)m;
+                    }
+                } else if (slot == 3) {
                     const float4 v = make_float4(o[0], o[1], o[2], o[3]);
                     if (DIRECT) {
                         const int dx = g.fx0 - g.ox + xo - 3;  // first column of the 4-vector
                         if (row_store && (unsigned)dx < (unsigned)g.lx) cvt_store4<T>(grow + (oo - 3), v);
+                        if (MAPS) {
+                            // the word's first column; a word that starts inside the frame may
+                            // spill into the row's padding bytes, never past the row pitch
+                            const int fx = g.fx0 + xo - 3;
+                            if (row_map && (unsigned)fx < (unsigned)g.FW)
+                                *reinterpret_cast<uint32_t *>(mplane + (long long)fy * g.MP + fx) = mw;
+                        }
                     } else if (row_ok) {
                         orow[oo >> 2] = v;
                     }
@@ -410,11 +428,11 @@ __device__ __forceinline__ void zero_outside(float *__restrict__ U, int pu, int 
 // ----------------------------------------------------------------------------------
 // the persistent kernel
 // ----------------------------------------------------------------------------------
-// DIRECT: one pass per launch whose results go from registers straight into the
-// destination frame (needs D == 1, EX == R and a frame destination); otherwise every
-// pass lands in shared memory and the tile interior is copied out at the end.
+// DIRECT: one pass per launch whose results (and selections, with MAPS) go from
+// registers straight into the destination (D == 1, halo EX == R); otherwise every pass
+// lands in shared memory and the tile interior is copied out at the end.
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
-__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
     const Layout2 L = make_layout2<T>(R, D, DIRECT);
@@ -467,7 +485,12 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(c
         // wait for this tile's region (bounded: a copy that never lands is reported, not waited on forever)
         const bool timed_out = !mbar_wait_bounded(bar, phase);
         if (__syncthreads_or(timed_out)) {
-            if (threadIdx.x == 0) atomicOr(p.err, 1u);
+            // report; thread 0 gives the copy one more bounded wait, so the CTA's shared
+            // memory outlives a copy that is merely late
+            if (threadIdx.x == 0) {
+                atomicOr(p.err, 1u);
+                mbar_wait_bounded(bar, phase);
+            }
             return;
         }
         phase ^= 1;
@@ -521,6 +544,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 ? 4 : 3) : 2) osbf_fwd2(c
             g.ox = g.oy;
             g.ly = p.dst_is_output ? p.H : p.FH;
             g.lx = p.dst_is_output ? p.W : p.FW;
+            g.MP = p.map_pitch;
             uint8_t *mplane = nullptr;
             if (MAPS && p.maps)
                 mplane =

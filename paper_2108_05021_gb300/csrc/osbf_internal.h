@@ -15,6 +15,9 @@ namespace osbf {
 
 enum class Storage { F32 = 0, F16 = 1, BF16 = 2, U8 = 3 };
 
+// row pitch (bytes) of the selection maps: frame width rounded up to 16 bytes
+inline int maps_pitch(int FW) { return (FW + 15) / 16 * 16; }
+
 // The exact first pass on 8-bit input (the first-pass tile kernel of osbf_fwd.cuh).
 cudaError_t launch_fwd_u8(int R, bool tie_app, const FwdParams &p, dim3 grid, cudaStream_t s);
 

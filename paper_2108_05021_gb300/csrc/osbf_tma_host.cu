@@ -24,7 +24,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // A 3-D map over P frames of FH rows x FW elements (row pitch `pitch` elements).  Reads
-// outside [0, FW) x [0, FH) return zeros -- the appendix's "zero outside the padded frame".
+// outside [0, FW) x [0, FH) return zeros -- the appendix's "zero outside the padded frame"
+// (for selection maps, U8: window index 0, "no window").
 bool encode_frame_map(CUtensorMap *map, Storage st, const void *base, int FW, int FH, int P, int pitch, int box_w,
                       int box_h) {
     auto fn = encode_fn();
@@ -37,6 +38,9 @@ bool encode_frame_map(CUtensorMap *map, Storage st, const void *base, int FW, in
     } else if (st == Storage::BF16) {
         dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
         es = 2;
+    } else if (st == Storage::U8) {
+        dt = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+        es = 1;
     }
     cuuint64_t dims[3] = {(cuuint64_t)FW, (cuuint64_t)FH, (cuuint64_t)P};
     cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)pitch * es * FH};

@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
         L.osbf_autotune.restype = st
         L.osbf_frame_pitch.argtypes = [i, i]
         L.osbf_frame_pitch.restype = i
+        L.osbf_maps_pitch.argtypes = [i, i]
+        L.osbf_maps_pitch.restype = i
         L.osbf_check.argtypes = [vp]
         L.osbf_check.restype = st
         L.osbf_batched_latencies.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), i]
@@ -155,9 +157,21 @@ def last_launch_count(device: int = 0) -> int:
     return lib().osbf_last_launch_count(context(device))
 
 
+def maps_pitch(W: int, r: int) -> int:
+    """Bytes per selection-map row: W + 2r rounded up to a multiple of 16."""
+    return lib().osbf_maps_pitch(W, r)
+
+
 def maps_shape(x: torch.Tensor, r: int, iters: int):
+    """Shape of the selection maps of osbf_filter_ex: (iters, N*C, H+2r, maps_pitch(W, r));
+    the first W+2r bytes of each row hold the window indices (maps_frames() views them)."""
     N, C, H, W = _nchw(x)
-    return (iters, N * C, H + 2 * r, W + 2 * r)
+    return (iters, N * C, H + 2 * r, maps_pitch(W, r))
+
+
+def maps_frames(maps, W: int, r: int):
+    """The frame columns of selection maps (a view without the row padding)."""
+    return maps[..., : W + 2 * r]
 
 
 def filter(x: torch.Tensor, r: int, iters: int, *, depth: int = 0, tie: str = "paper",
@@ -209,6 +223,8 @@ def backward(grad_out: torch.Tensor, maps: torch.Tensor, r: int, iters: int,
     if grad_out.dtype != torch.float32:
         raise TypeError("grad_out must be float32")
     N, C, H, W = _nchw(grad_out)
+    if maps.dtype != torch.uint8 or tuple(maps.shape) != maps_shape(grad_out, r, iters):
+        raise ValueError(f"maps must be uint8 of shape {maps_shape(grad_out, r, iters)}")
     if out is None:
         out = torch.empty_like(grad_out)
     dev = grad_out.device.index

@@ -56,3 +56,9 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(osbf, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         osbf.lib()
+
+
+def test_maps_pitch_rounds_frame_width_to_16_bytes(lib):
+    for W in (1, 7, 16, 100, 4096):
+        for r in (0, 1, 3, 8, 16):
+            assert lib.osbf_maps_pitch(W, r) == -(-(W + 2 * r) // 16) * 16

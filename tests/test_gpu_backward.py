@@ -25,7 +25,7 @@ def fwd_with_maps(x_np, r, iters):
 
 
 def check_adjoint(g_gpu, g_np, maps, r, iters):
-    want = oracle.adjoint(g_np.astype(np.float64), maps.cpu().numpy(), r, iters)
+    want = oracle.adjoint(g_np.astype(np.float64), osbf.maps_frames(maps, g_np.shape[-1], r).cpu().numpy(), r, iters)
     got = g_gpu.cpu().numpy().astype(np.float64)
     tol = 1e-5 * (1.0 + np.abs(want).max())
     err = np.abs(got - want).max()
@@ -33,7 +33,7 @@ def check_adjoint(g_gpu, g_np, maps, r, iters):
     return err
 
 
-@pytest.mark.parametrize("r", [1, 2, 3, 4, 8, 16])
+@pytest.mark.parametrize("r", list(range(1, 17)))
 @pytest.mark.parametrize("shape", [(1, 1, 70, 150), (2, 1, 33, 129)])
 def test_backward_matches_oracle_adjoint(shape, r):
     x_np = synth.piecewise_stack(*shape, seed=r, sigma=0.05)
@@ -116,7 +116,7 @@ def test_config5_sample():
     gy = (2.0 / y.numel()) * (y.detach() - torch.from_numpy(clean).to(DEV))
     planes = [0, 47]
     P = N * C
-    m = maps.cpu().numpy()
+    m = osbf.maps_frames(maps, W, r).cpu().numpy()
     for p in planes:
         want = oracle.adjoint(gy.reshape(P, H, W)[p].cpu().numpy().astype(np.float64), m[:, p:p + 1], r, iters)
         got = x.grad.reshape(P, H, W)[p].cpu().numpy()
@@ -126,10 +126,21 @@ def test_config5_sample():
 
 def test_backward_status_codes():
     g = torch.zeros(1, 1, 8, 8, device=DEV)
-    maps = torch.zeros(1, 1, 10, 10, dtype=torch.uint8, device=DEV)
     with pytest.raises(osbf.OSBFError) as e:
-        osbf.backward(g, maps, 17, 1)
+        osbf.backward(g, torch.zeros(osbf.maps_shape(g, 17, 1), dtype=torch.uint8, device=DEV), 17, 1)
     assert e.value.status_name == "OSBF_EUNSUPPORTED"
     with pytest.raises(osbf.OSBFError) as e:
-        osbf.backward(g, maps, -1, 1)
+        osbf.backward(g, torch.zeros(osbf.maps_shape(g, -1, 1), dtype=torch.uint8, device=DEV), -1, 1)
+    assert e.value.status_name == "OSBF_EINVAL"
+    # maps of the wrong shape are refused before any launch
+    with pytest.raises(ValueError):
+        osbf.backward(g, torch.zeros(1, 1, 10, 10, dtype=torch.uint8, device=DEV), 1, 1)
+    # maps must start on 16 bytes (the backward reads them with tensor copies)
+    buf = torch.zeros(osbf.maps_shape(g, 1, 1)[-1] * 10 + 16, dtype=torch.uint8, device=DEV)
+    with pytest.raises(osbf.OSBFError) as e:
+        lib, ctx = osbf.lib(), osbf.context(0)
+        gi = torch.empty_like(g)
+        st = lib.osbf_filter_backward(ctx, g.data_ptr(), gi.data_ptr(), buf.data_ptr() + 1, 1, 1, 8, 8, 1, 1,
+                                      osbf._stream(0))
+        osbf._check(st, ctx)
     assert e.value.status_name == "OSBF_EINVAL"

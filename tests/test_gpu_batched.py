@@ -48,7 +48,8 @@ def test_batched_replay_is_deterministic_and_matches_oracle():
     x = ins[k].cpu().numpy()
     maps = torch.zeros(osbf.maps_shape(ins[k], rs[k], its[k]), dtype=torch.uint8, device=DEV)
     osbf.filter(ins[k], rs[k], its[k], maps=maps)
-    ref = oracle.filter(x.astype(np.float64), rs[k], its[k], hint=maps.cpu().numpy(), hint_thresh=1e-6)["out"]
+    ref = oracle.filter(x.astype(np.float64), rs[k], its[k], hint=osbf.maps_frames(maps, x.shape[-1], rs[k]).cpu().numpy(),
+                       hint_thresh=1e-6)["out"]
     assert np.abs(a[k] - ref).max() <= 1e-5
 
 

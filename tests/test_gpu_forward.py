@@ -29,7 +29,7 @@ def gpu_filter(x_np, r, iters, depth=0, tie="paper", want_maps=True, dtype=torch
     maps = torch.zeros(osbf.maps_shape(x, r, iters), dtype=torch.uint8, device=DEV) if want_maps else None
     out = osbf.filter(x, r, iters, depth=depth, tie=tie, maps=maps)
     torch.cuda.synchronize()
-    return out.float().cpu().numpy(), (maps.cpu().numpy() if want_maps else None)
+    return out.float().cpu().numpy(), (osbf.maps_frames(maps, x.shape[-1], r).cpu().numpy() if want_maps else None)
 
 
 def check_f32(x_np, r, iters, depth=0, tie="paper"):
