@@ -192,23 +192,21 @@ template <> __device__ __forceinline__ void cvt_store4<__nv_bfloat16>(__nv_bfloa
 // ----------------------------------------------------------------------------------
 template <int R, int NRH>
 __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float *__restrict__ A, int pa, int RH_rt,
-                                        int RW, float *__restrict__ uc = nullptr) {
+                                        int RW) {
     constexpr int P = R + 1;
-    const int RH = NRH > 0 ? NRH : RH_rt;
-    const int pu_c = pa;  // the central-rows copy has the same pitch as A
     const int npairs = (RW + 1) >> 1;
     for (int item = threadIdx.x; item < npairs; item += NT) {
         const int c = item * 2;
         const float *col = U + c;
         float2 *acol = reinterpret_cast<float2 *>(A + c);
-        float2 *ucol = uc ? reinterpret_cast<float2 *>(uc + c) : nullptr;
         float2 ring[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) ring[k] = make_float2(0.f, 0.f);
         float2 acc = make_float2(0.f, 0.f);
-        auto step = [&](int s, int k) {
-            const float2 v = *reinterpret_cast<const float2 *>(col + s * pu);
-            if (k == P - 1) {  // the ring holds the whole window: re-form the sum
+        // one row: slide the window sum by the row entering (v) and the one leaving
+        // (ring[k]); once per ring period re-form it from the ring (bounded FP32 drift)
+        auto update = [&](float2 v, int k) {
+            if (k == P - 1) {
                 ring[k] = v;
                 acc = ring[0];
 #pragma unroll
@@ -217,17 +215,33 @@ __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, flo
                 acc = add2(acc, sub2(v, ring[k]));
                 ring[k] = v;
             }
-            if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
-            if (NRH > 0 && ucol && s >= R && s < R + TH) ucol[(s - R) * (pu_c >> 1)] = v;
         };
         if (NRH > 0) {
+            // loads run LA rows ahead in program order, so they never queue behind the
+            // column-sum stores of earlier rows (the compiler cannot reorder them itself)
+            constexpr int LA = 4;
+            constexpr int NR = NRH > 0 ? NRH : 1;
+            float2 q[LA];
 #pragma unroll
-            for (int s = 0; s < (NRH > 0 ? NRH : 1); ++s) step(s, s % P);
+            for (int i = 0; i < LA; ++i)
+                q[i] = i < NR ? *reinterpret_cast<const float2 *>(col + i * pu) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                const float2 v = q[s % LA];
+                if (s + LA < NR) q[s % LA] = *reinterpret_cast<const float2 *>(col + (s + LA) * pu);
+                update(v, s % P);
+                if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
+            }
         } else {
-            for (int s0 = 0; s0 < RH; s0 += P) {
+            for (int s0 = 0; s0 < RH_rt; s0 += P) {
 #pragma unroll
-                for (int k = 0; k < P; ++k)
-                    if (s0 + k < RH) step(s0 + k, k);
+                for (int k = 0; k < P; ++k) {
+                    const int s = s0 + k;
+                    if (s < RH_rt) {
+                        update(*reinterpret_cast<const float2 *>(col + s * pu), k);
+                        if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
+                    }
+                }
             }
         }
     }
@@ -311,7 +325,10 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         }
         float2 ABL = make_float2(0.f, 0.f);  // (AL, BL): left row sums of a and b
         float UL = 0.f;
-        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va, vu = va;
+        // loads run one 4-column group ahead in program order (ahead of this group's stores)
+        constexpr int NG = (NS + 3) / 4;
+        float4 va = arow[0], vb = brow[0], vu = urow[0];
+        float4 na = va, nb = vb, nu4 = vu;
         float o[4];
         uint32_t mw = 0;  // DIRECT maps: selections of the current 4-column group
         // the whole segment is unrolled: ring slots, loads, warm-up and stores are static
@@ -319,9 +336,14 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         for (int t = 0; t < NS; ++t) {
             const int k = t % P;
             if ((t & 3) == 0) {
-                va = arow[t >> 2];
-                vb = brow[t >> 2];
-                vu = urow[t >> 2];
+                va = na;
+                vb = nb;
+                vu = nu4;
+                if ((t >> 2) + 1 < NG) {
+                    na = arow[(t >> 2) + 1];
+                    nb = brow[(t >> 2) + 1];
+                    nu4 = urow[(t >> 2) + 1];
+                }
             }
             const float a = f4get(va, t & 3), b = f4get(vb, t & 3), u = f4get(vu, t & 3);
             if (t < R) {
@@ -428,6 +450,15 @@ __device__ __forceinline__ void zero_outside(float *__restrict__ U, int pu, int 
 // ----------------------------------------------------------------------------------
 // the persistent kernel
 // ----------------------------------------------------------------------------------
+// Tile order: plane by plane, row by row.
+__device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &plane, int &ty0, int &tx0) {
+    const int per = p.tiles_x * p.tiles_y;
+    plane = tile / per;
+    const int rem = tile - plane * per;
+    ty0 = (rem / p.tiles_x + p.ty_off) * TH;
+    tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
+}
+
 // DIRECT: one pass per launch whose results (and selections, with MAPS) go from
 // registers straight into the destination (D == 1, halo EX == R); otherwise every pass
 // lands in shared memory and the tile interior is copied out at the end.
@@ -444,7 +475,6 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
     const uint32_t bar = smem_u32(smem2 + L.bytes - 16);
     const int pu0 = sizeof(T) == 4 ? L.BX : L.PU;  // pitch of U^0 as a float buffer
 
-    const int tiles_per_plane = p.tiles_x * p.tiles_y;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -453,15 +483,15 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
     __syncthreads();
 
     auto issue = [&](int tile) {
-        const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
-        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
+        int plane, ty0, tx0;
+        tile_origin(p, tile, plane, ty0, tx0);
         tma_load_3d(smem_u32(bin), &src, tx0 - L.EX, ty0 - L.EY, plane, bar, (uint32_t)L.in_bytes);
     };
     // L2 prefetch of a tile's box: issued one tile ahead of its shared-memory load, so
     // that load is served from L2 instead of DRAM
     auto warm = [&](int tile) {
-        const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
-        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
+        int plane, ty0, tx0;
+        tile_origin(p, tile, plane, ty0, tx0);
         tma_prefetch_l2_3d(&src, tx0 - L.EX, ty0 - L.EY, plane);
     };
     auto prefetch = [&](int tile) {
@@ -480,8 +510,8 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
     }
     uint32_t phase = 0;
     for (; tile < p.ntiles; tile += gridDim.x) {
-        const int plane = tile / tiles_per_plane, rem = tile % tiles_per_plane;
-        const int ty0 = (rem / p.tiles_x + p.ty_off) * TH, tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
+        int plane, ty0, tx0;
+        tile_origin(p, tile, plane, ty0, tx0);
         // wait for this tile's region (bounded: a copy that never lands is reported, not waited on forever)
         const bool timed_out = !mbar_wait_bounded(bar, phase);
         if (__syncthreads_or(timed_out)) {
@@ -516,19 +546,11 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
             const int puin = j == 1 ? pu0 : L.PU;
             float *Uout = (j & 1) ? Ua : Ub;
             const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
-            // direct float32 kernels: pass V also copies the pixel rows of U, so the TMA box
-            // is dead after pass V and the next tile's load overlaps pass H
-            constexpr bool UCOPY = false;  // a central-row copy frees the box early but costs a CTA per SM
-            float *uc = reinterpret_cast<float *>(smem2 + L.off_uf);
             if (DIRECT)
-                pass_v2<R, TH + 2 * R>(Uin, puin, A, L.P2, RH, RW, UCOPY ? uc : nullptr);
+                pass_v2<R, TH + 2 * R>(Uin, puin, A, L.P2, RH, RW);
             else
                 pass_v2<R, 0>(Uin, puin, A, L.P2, RH, RW);
             __syncthreads();
-            if (UCOPY && !prefetched) {
-                prefetch(tile);
-                prefetched = true;
-            }
             Geom2 g;
             g.RHo = RH - 2 * R;
             g.RWo = RW - 2 * R;
@@ -549,10 +571,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            if (UCOPY)
-                pass_h2<R, T, TIE_APP, MAPS, DIRECT>(uc, L.P2, 0, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
-            else
-                pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
