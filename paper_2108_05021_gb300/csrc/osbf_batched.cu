@@ -1,15 +1,22 @@
 // Batched form: many single-plane float32 images of different sizes, radii and pass
 // counts in ONE persistent launch, replayed from a CUDA graph cached per job signature.
 //
-// Work items are (job, pass group, tile), listed round by round: every job's group-0
-// tiles, then every job's group-1 tiles, and so on.  CTAs take items in that order from
-// a global counter; an item of group g first waits until all tiles of its job's group
-// g-1 are done (a per-(job, group) counter).  Every item listed before it has already
-// been taken by a resident CTA, so the wait always ends; it is bounded all the same
-// (a limit of 2 s, after which the kernel records an error that osbf_filter_batched
-// returns as OSBF_ETIMEOUT).  The sweep code is the forward's (osbf_fwd2.cuh), selected
-// per item by a switch on the radius; loads are plain 16-byte L2 loads (each job has its
-// own buffers, so no per-job tensor maps are needed).
+// Work items are (job, pass, tile, kind), listed round by round: every job's pass-0
+// tiles, then every job's pass-1 tiles, and so on; after a job's last pass come its crop
+// items (kind 1), which copy the frame's interior into the job's output.  CTAs take items
+// in that order from a global counter; an item of pass g first waits until all tiles of
+// its job's pass g-1 are done (a per-(job, pass) counter).  Every item listed before it
+// has already been taken by a resident CTA, so the wait always ends; it is bounded all
+// the same (2 s by default, after which the kernel records an error that
+// osbf_filter_batched returns as OSBF_ETIMEOUT).
+//
+// One item is one pass over one tile with the forward's single-pass machinery
+// (osbf_fwd2.cuh): the tile's region (tile + r halo) is loaded into shared memory --
+// pass 0 from the replicate-padded input by clamped reads, later passes from the job's
+// previous frame by coalesced 16-byte L2 loads (another SM wrote it) -- and pass H
+// writes its results from registers straight into the job's next frame.  Both loads are
+// flat loops over the region's elements.  The sweep code is selected per item by a
+// switch on the radius.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -25,7 +32,6 @@ void osbf_ctx_reset_launches(osbf_ctx *ctx);
 int osbf_ctx_sms(const osbf_ctx *ctx);
 int osbf_ctx_device(const osbf_ctx *ctx);
 void **osbf_ctx_batch_state(osbf_ctx *ctx);
-int osbf_ctx_tuned_depth(osbf_ctx *ctx, osbf_dtype dt, int r, long long pixels);
 unsigned long long osbf_ctx_wait_ns(const osbf_ctx *ctx);
 osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int in_pitch, void *out, int out_is_frame,
                              int out_pitch, int P, int H, int W, int r, int iters, osbf_dtype dtype, int depth,
@@ -40,19 +46,20 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 struct Job {
     const float *in;
     float *out;
-    float *frame[2];
-    int H, W, FH, FW, FWp, R, D, iters, ngroups, tiles_x, ntiles, cnt_base;
+    float *frame[2];  // pass g writes frame[g & 1]
+    int H, W, FH, FW, FWp, R, iters, tiles_x, ntiles, cnt_base;
+    int shift;        // tile k starts at frame column k * TW - shift (TMA boxes start on 16 bytes)
 };
 
 struct Params {
     unsigned long long wait_ns;  // bound of the dependency wait
     const Job *jobs;
-    const int4 *items;  // (job, group, tile, -)
+    const int4 *items;           // (job, pass, tile, kind)
     int nitems;
-    int *next;          // item counter
-    int *done;          // tiles finished per (job, group)
+    int *next;                   // item counter
+    int *done;                   // tiles finished per (job, pass); the crop is pass `iters`
     unsigned int *err;
-    unsigned long long *t_done;  // per job: globaltimer when its last tile finished
+    unsigned long long *t_done;  // per job: globaltimer when its last crop tile finished
     unsigned long long *t_start;
 };
 
@@ -62,92 +69,89 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
-// U^0 region of the tile into shared memory: the replicate-padded input (group 0) or the
-// job's previous frame (later groups; L2 loads, since another SM wrote it), zero outside.
-__device__ void load_region(const Job &jb, int g, const v2::Layout2 &L, float *U0, int ty0, int tx0) {
+// Pass 0's region: the replicate-padded input (clamped reads), zero outside the frame.
+// One flat loop over the box's elements (row-major, consecutive threads on consecutive
+// columns).
+__device__ void load_padded_input(const Job &jb, const v2::Layout2 &L, float *box, int ty0, int tx0) {
     const int fy0 = ty0 - L.EY, fx0 = tx0 - L.EX;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (g == 0) {
-        for (int y = warp; y < L.RH0; y += v2::NT / 32) {
-            const int fy = fy0 + y;
-            const bool yin = (unsigned)fy < (unsigned)jb.FH;
-            const float *srow = jb.in + (long long)min(max(fy - jb.R, 0), jb.H - 1) * jb.W;
-            for (int x = lane; x < L.BX; x += 32) {
-                const int fx = fx0 + x;
-                float v = 0.f;
-                if (yin && (unsigned)fx < (unsigned)jb.FW) v = __ldg(srow + min(max(fx - jb.R, 0), jb.W - 1));
-                U0[y * L.BX + x] = v;
-            }
-        }
-    } else {
-        const float *src = jb.frame[(g - 1) & 1];
-        const int nv = L.BX / 4;
-        for (int i = threadIdx.x; i < L.RH0 * nv; i += v2::NT) {
-            const int y = i / nv, x = (i % nv) * 4;
-            const int fy = fy0 + y, fx = fx0 + x;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if ((unsigned)fy < (unsigned)jb.FH && fx >= 0 && fx < jb.FW) {
-                v = __ldcg(reinterpret_cast<const float4 *>(src + (long long)fy * jb.FWp + fx));
-                if (fx + 1 >= jb.FW) v.y = 0.f;
-                if (fx + 2 >= jb.FW) v.z = 0.f;
-                if (fx + 3 >= jb.FW) v.w = 0.f;
-            }
-            *reinterpret_cast<float4 *>(U0 + y * L.BX + x) = v;
-        }
+    const int n = L.RH0 * L.BX;
+    for (int e = threadIdx.x; e < n; e += v2::NT) {
+        const int y = e / L.BX, x = e - y * L.BX;
+        const int fy = fy0 + y, fx = fx0 + x;
+        float v = 0.f;
+        if ((unsigned)fy < (unsigned)jb.FH && (unsigned)fx < (unsigned)jb.FW)
+            v = jb.in[(long long)min(max(fy - jb.R, 0), jb.H - 1) * jb.W + min(max(fx - jb.R, 0), jb.W - 1)];
+        box[e] = v;
     }
 }
 
+// Later passes' region: the job's previous frame, zero outside it.  The region starts on
+// a 16-byte boundary (the tile grid is shifted so that tx0 - r is a multiple of 4), so
+// every 4-vector is either wholly left of the frame or starts inside a row; elements past
+// the frame's last column are zeroed (the row pitch keeps the vector in bounds).
+__device__ void load_frame_region(const Job &jb, const float *src, const v2::Layout2 &L, float *box, int ty0,
+                                  int tx0) {
+    const int fy0 = ty0 - L.EY, fx0 = tx0 - L.EX;
+    const int nv = L.BX / 4;
+    const int n = L.RH0 * nv;
+    for (int e = threadIdx.x; e < n; e += v2::NT) {
+        const int y = e / nv, x = (e - y * nv) * 4;
+        const int fy = fy0 + y, fx = fx0 + x;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned)fy < (unsigned)jb.FH && fx >= 0 && fx < jb.FW) {
+            v = __ldcg(reinterpret_cast<const float4 *>(src + (long long)fy * jb.FWp + fx));
+            if (fx + 1 >= jb.FW) v.y = 0.f;
+            if (fx + 2 >= jb.FW) v.z = 0.f;
+            if (fx + 3 >= jb.FW) v.w = 0.f;
+        }
+        *reinterpret_cast<float4 *>(box + y * L.BX + x) = v;
+    }
+}
+
+// One pass over one tile.
 template <int R>
 __device__ void process(const Job &jb, int g, int tile, unsigned char *smem) {
-    const int D = g == jb.ngroups - 1 ? jb.iters - g * jb.D : jb.D;
-    const v2::Layout2 L = v2::make_layout2<float>(R, D);
-    float *U0 = reinterpret_cast<float *>(smem + L.off_in);
+    const v2::Layout2 L = v2::make_layout2<float>(R, 1, true);
+    float *box = reinterpret_cast<float *>(smem + L.off_in);
     float *A = reinterpret_cast<float *>(smem + L.off_ab);
-    float *Ua = reinterpret_cast<float *>(smem + L.off_ua);
-    float *Ub = reinterpret_cast<float *>(smem + L.off_ub);
-    const int ty0 = (tile / jb.tiles_x) * v2::TH, tx0 = (tile % jb.tiles_x) * v2::TW;
-    load_region(jb, g, L, U0, ty0, tx0);
+    const int ty0 = (tile / jb.tiles_x) * v2::TH;
+    const int tx0 = (tile % jb.tiles_x) * v2::TW - jb.shift;
+    if (g == 0)
+        load_padded_input(jb, L, box, ty0, tx0);
+    else
+        load_frame_region(jb, jb.frame[(g - 1) & 1], L, box, ty0, tx0);
     __syncthreads();
-    const bool interior =
-        ty0 - L.EY >= 0 && tx0 - L.EX >= 0 && ty0 + v2::TH + L.EY <= jb.FH && tx0 + v2::TW + L.EX <= jb.FW;
-    for (int j = 1; j <= D; ++j) {
-        const float *Uin = j == 1 ? U0 : ((j & 1) ? Ub : Ua);
-        const int puin = j == 1 ? L.BX : L.PU;
-        float *Uout = (j & 1) ? Ua : Ub;
-        const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
-        v2::pass_v2<R, 0>(Uin, puin, A, L.P2, RH, RW);
-        __syncthreads();
-        v2::Geom2 gm;
-        gm.RHo = RH - 2 * R;
-        gm.RWo = RW - 2 * R;
-        gm.fy0 = ty0 - (L.EY - j * R);
-        gm.fx0 = tx0 - (L.EX - j * R);
-        gm.FH = jb.FH;
-        gm.FW = jb.FW;
-        gm.iy0 = gm.iy1 = gm.ix0 = gm.ix1 = 0;
-        gm.oy = gm.ox = gm.ly = gm.lx = 0;
-        v2::pass_h2<R, float, false, false, false>(Uin, puin, R, A, L.P2, Uout, L.PU, nullptr, 0, gm, nullptr);
-        __syncthreads();
-        if (j < D && !interior) {
-            v2::zero_outside(Uout, L.PU, gm.RHo, gm.RWo, gm.fy0, gm.fx0, jb.FH, jb.FW);
-            __syncthreads();
-        }
-    }
-    const float *UD = (D & 1) ? Ua : Ub;
-    const int cx = L.EX - D * R;
-    if (g < jb.ngroups - 1) {
-        float *dst = jb.frame[g & 1];
-        for (int i = threadIdx.x; i < v2::TH * v2::TW; i += v2::NT) {
-            const int y = i / v2::TW, x = i % v2::TW;
-            const int fy = ty0 + y, fx = tx0 + x;
-            if (fy < jb.FH && fx < jb.FW) dst[(long long)fy * jb.FWp + fx] = UD[y * L.PU + cx + x];
-        }
-    } else {
-        for (int i = threadIdx.x; i < v2::TH * v2::TW; i += v2::NT) {
-            const int y = i / v2::TW, x = i % v2::TW;
-            const int oy = ty0 + y - jb.R, ox = tx0 + x - jb.R;
-            if (oy >= 0 && oy < jb.H && ox >= 0 && ox < jb.W) jb.out[(long long)oy * jb.W + ox] = UD[y * L.PU + cx + x];
-        }
+    v2::pass_v2<R, v2::TH + 2 * R>(box, L.BX, A, L.P2, L.RH0, L.RW0);
+    __syncthreads();
+    v2::Geom2 gm;
+    gm.RHo = v2::TH;
+    gm.RWo = v2::TW;
+    gm.fy0 = ty0;
+    gm.fx0 = tx0;
+    gm.FH = jb.FH;
+    gm.FW = jb.FW;
+    gm.iy0 = 0;
+    gm.iy1 = v2::TH;
+    gm.ix0 = 0;
+    gm.ix1 = v2::TW;
+    gm.oy = gm.ox = 0;
+    gm.ly = jb.FH;
+    gm.lx = jb.FW;
+    gm.MP = 0;
+    v2::pass_h2<R, float, false, false, true>(box, L.BX, R, A, L.P2, nullptr, 0, jb.frame[g & 1], jb.FWp, gm,
+                                              nullptr);
+}
+
+// The crop: the interior of the last frame into the job's output (coalesced rows).
+__device__ void crop(const Job &jb, int tile) {
+    const int ty0 = (tile / jb.tiles_x) * v2::TH;
+    const int tx0 = (tile % jb.tiles_x) * v2::TW - jb.shift;
+    const float *src = jb.frame[(jb.iters - 1) & 1];
+    for (int i = threadIdx.x; i < v2::TH * v2::TW; i += v2::NT) {
+        const int fy = ty0 + i / v2::TW, fx = tx0 + i % v2::TW;
+        const int oy = fy - jb.R, ox = fx - jb.R;
+        if ((unsigned)oy < (unsigned)jb.H && (unsigned)ox < (unsigned)jb.W)
+            jb.out[(long long)oy * jb.W + ox] = __ldcg(src + (long long)fy * jb.FWp + fx);
     }
 }
 
@@ -159,6 +163,7 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
         atomicMin(p.t_start, now_ns());
         s_fail = 0;
     }
+    __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(p.next, 1);
         __syncthreads();
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
         const Job jb = p.jobs[it.x];
         const int g = it.y;
         if (threadIdx.x == 0 && g > 0) {
-            // the job's previous group must be complete (bounded wait)
+            // the job's previous pass must be complete (bounded wait)
             const volatile int *cnt = p.done + jb.cnt_base + g - 1;
             const unsigned long long t0 = now_ns();
             while (*cnt < jb.ntiles) {
@@ -177,27 +182,33 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
                     s_fail = 1;
                     break;
                 }
-                __nanosleep(256);
+                __nanosleep(128);
             }
             __threadfence();
         }
         __syncthreads();
         if (s_fail) break;
-        switch (jb.R) {
-        case 1: process<1>(jb, g, it.z, bsmem); break;
-        case 2: process<2>(jb, g, it.z, bsmem); break;
-        case 3: process<3>(jb, g, it.z, bsmem); break;
-        case 4: process<4>(jb, g, it.z, bsmem); break;
-        case 5: process<5>(jb, g, it.z, bsmem); break;
-        case 6: process<6>(jb, g, it.z, bsmem); break;
-        case 7: process<7>(jb, g, it.z, bsmem); break;
-        default: process<8>(jb, g, it.z, bsmem); break;
+        if (it.w) {
+            crop(jb, it.z);
+        } else {
+            switch (jb.R) {
+            case 1: process<1>(jb, g, it.z, bsmem); break;
+            case 2: process<2>(jb, g, it.z, bsmem); break;
+            case 3: process<3>(jb, g, it.z, bsmem); break;
+            case 4: process<4>(jb, g, it.z, bsmem); break;
+            case 5: process<5>(jb, g, it.z, bsmem); break;
+            case 6: process<6>(jb, g, it.z, bsmem); break;
+            case 7: process<7>(jb, g, it.z, bsmem); break;
+            default: process<8>(jb, g, it.z, bsmem); break;
+            }
         }
+        // a fence orders only its own thread's writes: every thread publishes its stores
+        // of this tile before the tile is counted
+        __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();  // this tile's results are visible before it is counted
             const int prev = atomicAdd(p.done + jb.cnt_base + g, 1);
-            if (prev + 1 == jb.ntiles && g == jb.ngroups - 1) p.t_done[it.x] = now_ns();
+            if (it.w && prev + 1 == jb.ntiles) p.t_done[it.x] = now_ns();
         }
     }
 }
@@ -275,8 +286,7 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
             if (e) return e;
         } else {
             pj.push_back(j);
-            sig.insert(sig.end(), {(long long)(uintptr_t)q.in, (long long)(uintptr_t)q.out, q.H, q.W, q.r, q.iters,
-                                   osbf_ctx_tuned_depth(ctx, OSBF_F32, q.r, (long long)q.H * q.W)});
+            sig.insert(sig.end(), {(long long)(uintptr_t)q.in, (long long)(uintptr_t)q.out, q.H, q.W, q.r, q.iters});
         }
     }
     if (pj.empty()) return OSBF_OK;
@@ -286,7 +296,7 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
         // ---- plan: jobs, items in round order, counters, arena ----
         std::vector<batched::Job> hj(pj.size());
         size_t frame_floats = 0;
-        int cnt = 0, max_groups = 0;
+        int cnt = 0, max_iters = 0;
         size_t smem = 0;
         for (size_t k = 0; k < pj.size(); ++k) {
             const osbf_job &q = jobs[pj[k]];
@@ -300,27 +310,20 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
             b.FW = q.W + 2 * q.r;
             b.FWp = (b.FW + 31) / 32 * 32;
             b.iters = q.iters;
-            int D = osbf_ctx_tuned_depth(ctx, OSBF_F32, q.r, (long long)q.H * q.W);
-            while (D > 1 && (size_t)v2::make_layout2<float>(q.r, D).bytes > 200 * 1024) --D;
-            if (D > q.iters) D = q.iters;
-            b.D = D;
-            b.ngroups = (q.iters + D - 1) / D;
-            b.tiles_x = (b.FW + v2::TW - 1) / v2::TW;
+            b.shift = (4 - q.r % 4) % 4;
+            b.tiles_x = (b.FW - 1 + b.shift) / v2::TW + 1;
             b.ntiles = b.tiles_x * ((b.FH + v2::TH - 1) / v2::TH);
             b.cnt_base = cnt;
-            cnt += b.ngroups;
-            max_groups = std::max(max_groups, b.ngroups);
-            frame_floats += (b.ngroups > 1 ? (b.ngroups > 2 ? 2 : 1) : 0) * (size_t)b.FH * b.FWp;
-            for (int g = 0; g < b.ngroups; ++g) {
-                const int Dg = g == b.ngroups - 1 ? q.iters - g * D : D;
-                smem = std::max(smem, (size_t)v2::make_layout2<float>(q.r, Dg).bytes);
-            }
+            cnt += b.iters + 1;  // the passes, then the crop
+            max_iters = std::max(max_iters, b.iters);
+            frame_floats += 2 * (size_t)b.FH * b.FWp;
+            smem = std::max(smem, (size_t)v2::make_layout2<float>(q.r, 1, true).bytes);
         }
         std::vector<int4> items;
-        for (int g = 0; g < max_groups; ++g)
+        for (int g = 0; g <= max_iters; ++g)
             for (size_t k = 0; k < hj.size(); ++k)
-                if (g < hj[k].ngroups)
-                    for (int t = 0; t < hj[k].ntiles; ++t) items.push_back(make_int4((int)k, g, t, 0));
+                if (g <= hj[k].iters)
+                    for (int t = 0; t < hj[k].ntiles; ++t) items.push_back(make_int4((int)k, g, t, g == hj[k].iters));
         // arena: jobs | items | next | counters | err | t_done | t_start | frames
         size_t off = 0;
         auto take = [&](size_t bytes) {
@@ -342,17 +345,11 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
             return osbf_ctx_fail(ctx, OSBF_ENOMEM, "batched arena allocation failed");
         }
         float *fr = (float *)(arena + o_frames);
-        for (auto &b : hj) {
-            b.frame[0] = b.frame[1] = nullptr;
-            if (b.ngroups > 1) {
-                b.frame[0] = fr;
+        for (auto &b : hj)
+            for (int f = 0; f < 2; ++f) {
+                b.frame[f] = fr;
                 fr += (size_t)b.FH * b.FWp;
             }
-            if (b.ngroups > 2) {
-                b.frame[1] = fr;
-                fr += (size_t)b.FH * b.FWp;
-            }
-        }
         if (cudaMemcpy(arena + o_jobs, hj.data(), sizeof(batched::Job) * hj.size(), cudaMemcpyHostToDevice) !=
                 cudaSuccess ||
             cudaMemcpy(arena + o_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
@@ -425,7 +422,7 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
     if (cudaMemcpyAsync(&w, pl.err, sizeof w, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return osbf_ctx_fail(ctx, OSBF_ECUDA, "batched launch failed");
-    if (w) return osbf_ctx_fail(ctx, OSBF_ETIMEOUT, "a batched item waited too long for its previous pass group");
+    if (w) return osbf_ctx_fail(ctx, OSBF_ETIMEOUT, "a batched item waited too long for its previous pass");
     return OSBF_OK;
 }
 
