@@ -49,7 +49,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one forward launch of the headline workload, from one ncu
 # capture of that launch (to be reset to None whenever the kernel changes)
-TRAFFIC_PER_LAUNCH = 358.6e6
+TRAFFIC_PER_LAUNCH = 359.0e6
 
 
 def hbm_peak():
