@@ -20,11 +20,21 @@
  * Arithmetic is FP64 (int64 for the exact 8-bit rule).  Window sums are direct
  * summations over the window, no running sums, no integral images.
  *
+ *   - the fast approximation of Sec. "Fast Approximation to One-sided Box Filter"
+ *     (Algorithm 3, Eq. (app)): one quadrant-mean field per pass, the other three
+ *     quadrants read from it at shifts of r, the four half windows approximated by
+ *     the mean of their two quadrant means (oracle_fast_iterate_frame_f64).
  * Readings of the paper taken here (the paper is silent or self-inconsistent):
  *   - `iters` passes (the appendix's `for it = 1:ItNum`), not IterationNum+1;
  *   - tie order "paper": N1..N8; tie order "appendix": the appendix's difference
  *     planes, i.e. N6, N5, N7, N8, N2, N1, N3, N4;
- *   - the updated value is the selected mean itself (U + d_m in exact arithmetic).
+ *   - the updated value is the selected mean itself (U + d_m in exact arithmetic);
+ *   - fast approximation: the base field is k_1's mean (window N1: rows y..y+r, cols
+ *     x-r..x), so with rows increasing downward the shifts that give N2, N4, N3 are
+ *     (0, +r), (-r, 0), (-r, +r) in (row, column); N5 ~ (a4 + a1)/2, N6 ~ (a3 + a2)/2,
+ *     N7 ~ (a1 + a2)/2 (the paper's example), N8 ~ (a4 + a3)/2; selection, update,
+ *     tie orders and boundary as in Algorithm 2 (the garbled argmin and update lines of
+ *     Algorithm 3 read this way).
  */
 #include <math.h>
 #include <stdint.h>
@@ -258,6 +268,105 @@ int oracle_filter_f64(const double *in, double *out, int P, int H, int W, int r,
     oracle_pad_replicate_f64(in, frame, P, H, W, r);
     int st = oracle_iterate_frame_f64(frame, P, FH, FW, r, iters, tie, maps, gaps, hint, hint_thresh,
                                       n_hinted, storage);
+    if (st == ORACLE_OK) oracle_crop_f64(frame, out, P, H, W, r);
+    free(frame);
+    return st;
+}
+
+/*
+ * The fast approximation (Sec. "Fast Approximation to One-sided Box Filter",
+ * Algorithm 3, Eq. (app)), `iters` passes on padded frames, in place.  Per pass:
+ *   1. one convolution: D(y, x) = mean of U over N1(y, x) (rows y..y+r, cols x-r..x),
+ *      zeros outside the frame, evaluated wherever a lookup below needs it (rows -r..FH-1);
+ *   2. the quadrant means by lookup: a1 = D(y, x), a2 = D(y, x+r), a4 = D(y-r, x),
+ *      a3 = D(y-r, x+r);
+ *   3. the half windows by Eq. (app): a5 = (a4+a1)/2, a6 = (a3+a2)/2, a7 = (a1+a2)/2,
+ *      a8 = (a4+a3)/2;
+ *   4. d_i = a_i - U, first argmin |d_i| in the tie order, U' = a_m (Jacobi).
+ * maps / gaps / hint / n_hinted as in oracle_iterate_frame_f64.
+ */
+int oracle_fast_iterate_frame_f64(double *frame, int P, int FH, int FW, int r, int iters, int tie, uint8_t *maps,
+                                  double *gaps, const uint8_t *hint, double hint_thresh, long long *n_hinted) {
+    if (P <= 0 || FH <= 0 || FW <= 0 || r < 0 || iters < 0 || tie < 0 || tie > 1) return ORACLE_EINVAL;
+    size_t plane = (size_t)FH * FW, total = (size_t)P * plane;
+    /* D on rows -r..FH-1 and columns 0..FW-1+r */
+    const int DH = FH + r, DW = FW + r;
+    double *next = (double *)malloc(sizeof(double) * (total ? total : 1));
+    double *D = (double *)malloc(sizeof(double) * (size_t)P * DH * DW);
+    if (!next || !D) {
+        free(next);
+        free(D);
+        return ORACLE_ENOMEM;
+    }
+    const int *order = TIE_ORDER[tie];
+    const double nq = (double)window_count(1, r);
+    long long hinted = 0;
+    for (int t = 0; t < iters; ++t) {
+        /* step 1: the one convolution */
+#pragma omp parallel for schedule(static)
+        for (long row = 0; row < (long)P * DH; ++row) {
+            int p = (int)(row / DH), yy = (int)(row % DH) - r;
+            const double *V = frame + (size_t)p * plane;
+            for (int x = 0; x < DW; ++x)
+                D[(size_t)p * DH * DW + (size_t)(yy + r) * DW + x] = window_sum_f64(V, FH, FW, yy, x, 1, r) / nq;
+        }
+        /* steps 2-4 */
+#pragma omp parallel for schedule(static) reduction(+ : hinted)
+        for (long row = 0; row < (long)P * FH; ++row) {
+            int p = (int)(row / FH), y = (int)(row % FH);
+            const double *V = frame + (size_t)p * plane;
+            const double *Dp = D + (size_t)p * DH * DW;
+            for (int x = 0; x < FW; ++x) {
+                size_t idx = (size_t)p * plane + (size_t)y * FW + x;
+                double u = V[(size_t)y * FW + x];
+                double a[9], ad[9];
+                a[1] = Dp[(size_t)(y + r) * DW + x];           /* D(y, x)     */
+                a[2] = Dp[(size_t)(y + r) * DW + x + r];       /* D(y, x+r)   */
+                a[4] = Dp[(size_t)y * DW + x];                 /* D(y-r, x)   */
+                a[3] = Dp[(size_t)y * DW + x + r];             /* D(y-r, x+r) */
+                a[5] = 0.5 * (a[4] + a[1]);
+                a[6] = 0.5 * (a[3] + a[2]);
+                a[7] = 0.5 * (a[1] + a[2]);
+                a[8] = 0.5 * (a[4] + a[3]);
+                for (int i = 1; i <= 8; ++i) ad[i] = fabs(a[i] - u);
+                int m = order[0];
+                for (int k = 1; k < 8; ++k)
+                    if (ad[order[k]] < ad[m]) m = order[k];
+                double gap = INFINITY;
+                for (int i = 1; i <= 8; ++i)
+                    if (i != m && a[i] != a[m] && ad[i] - ad[m] < gap) gap = ad[i] - ad[m];
+                size_t tidx = (size_t)t * total + idx;
+                if (hint) {
+                    int h = hint[tidx];
+                    if (h >= 1 && h <= 8 && h != m && ad[h] - ad[m] < hint_thresh) {
+                        if (a[h] != a[m]) hinted += 1;
+                        m = h;
+                    }
+                }
+                next[idx] = a[m];
+                if (maps) maps[tidx] = (uint8_t)m;
+                if (gaps) gaps[tidx] = gap;
+            }
+        }
+        memcpy(frame, next, sizeof(double) * total);
+    }
+    free(next);
+    free(D);
+    if (n_hinted) *n_hinted = hinted;
+    return ORACLE_OK;
+}
+
+/* The fast approximation on P planes of H x W: pad, iterate, crop (the appendix's boundary). */
+int oracle_fast_filter_f64(const double *in, double *out, int P, int H, int W, int r, int iters, int tie,
+                           uint8_t *maps, double *gaps, const uint8_t *hint, double hint_thresh,
+                           long long *n_hinted) {
+    if (P <= 0 || H <= 0 || W <= 0 || r < 0 || iters < 0) return ORACLE_EINVAL;
+    int FH = H + 2 * r, FW = W + 2 * r;
+    double *frame = (double *)malloc(sizeof(double) * (size_t)P * FH * FW);
+    if (!frame) return ORACLE_ENOMEM;
+    oracle_pad_replicate_f64(in, frame, P, H, W, r);
+    int st = oracle_fast_iterate_frame_f64(frame, P, FH, FW, r, iters, tie, maps, gaps, hint, hint_thresh,
+                                           n_hinted);
     if (st == ORACLE_OK) oracle_crop_f64(frame, out, P, H, W, r);
     free(frame);
     return st;

@@ -390,3 +390,96 @@ def test_storage_rounded_filter_stays_on_grid():
     x = synth.round_to_storage(synth.piecewise_plane(20, 20, seed=2), "f16").astype(np.float64)
     out = oracle.filter(x, 2, 3, storage="f16")["out"]
     np.testing.assert_array_equal(oracle.round_storage(out, "f16"), out)
+
+
+# ---------------------------------------------------------------------------------
+# The fast approximation (Sec. "Fast Approximation to One-sided Box Filter",
+# Algorithm 3, Eq. (app)).
+# ---------------------------------------------------------------------------------
+def _fast_brute(img, r, iters, tie="paper"):
+    """Pure-Python restatement: replicate pad, per pass the four quadrant means taken
+    directly from their pixel sets (not by shifted lookups), the half windows as the mean
+    of their two quadrants, first argmin in the tie order, Jacobi update, crop."""
+    H, W = len(img), len(img[0])
+    FH, FW = H + 2 * r, W + 2 * r
+    V = [[img[min(max(y - r, 0), H - 1)][min(max(x - r, 0), W - 1)] for x in range(FW)] for y in range(FH)]
+    order = [1, 2, 3, 4, 5, 6, 7, 8] if tie == "paper" else [6, 5, 7, 8, 2, 1, 3, 4]
+    quads = {1: (0, r, -r, 0), 2: (0, r, 0, r), 3: (-r, 0, 0, r), 4: (-r, 0, -r, 0)}  # rows, cols
+    n = (r + 1) ** 2
+    for _ in range(iters):
+        nxt = [[0.0] * FW for _ in range(FH)]
+        for y in range(FH):
+            for x in range(FW):
+                a = {}
+                for k, (y0, y1, x0, x1) in quads.items():
+                    s = 0.0
+                    for yy in range(y + y0, y + y1 + 1):
+                        for xx in range(x + x0, x + x1 + 1):
+                            if 0 <= yy < FH and 0 <= xx < FW:
+                                s += V[yy][xx]
+                    a[k] = s / n
+                a[5] = (a[4] + a[1]) / 2
+                a[6] = (a[3] + a[2]) / 2
+                a[7] = (a[1] + a[2]) / 2
+                a[8] = (a[4] + a[3]) / 2
+                u = V[y][x]
+                m = order[0]
+                for k in order[1:]:
+                    if abs(a[k] - u) < abs(a[m] - u):
+                        m = k
+                nxt[y][x] = a[m]
+        V = nxt
+    return np.array([[V[y + r][x + r] for x in range(W)] for y in range(H)])
+
+
+@pytest.mark.parametrize("r,iters,tie", [(1, 1, "paper"), (1, 3, "appendix"), (2, 2, "paper"), (3, 1, "appendix")])
+def test_fast_oracle_matches_brute_force(r, iters, tie):
+    rng = np.random.default_rng(100 + r * 10 + iters)
+    img = rng.random((7, 9))
+    got = oracle.fast_filter(img, r, iters, tie=tie)["out"]
+    want = _fast_brute(img.tolist(), r, iters, tie)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("r", [1, 3])
+@pytest.mark.parametrize("alpha,beta,tie,win", [
+    (1, 3, "paper", 5),      # |d| = r/2 * (2, 4, 2, 4, 1, 1, 3, 3): N5 first
+    (1, 3, "appendix", 6),   # N6 precedes N5 in the appendix order
+    (3, 1, "paper", 7),      # |d| = r/2 * (2, 4, 2, 4, 3, 3, 1, 1): N7 first
+    (3, 1, "appendix", 7),
+])
+def test_fast_linear_ramp_closed_form(alpha, beta, tie, win, r):
+    """On U = alpha x + beta y the quadrant means are U + r/2 (-alpha + beta, alpha + beta,
+    alpha - beta, -alpha - beta) (N1..N4), and Eq. (app) gives the half windows
+    U + r/2 (-alpha, alpha, beta, -beta) (N5..N8) -- which, for a linear image, are also the
+    exact half-window means, so the fast and the exact filter agree.  Interior pixels
+    (all windows inside the image) move by the first smallest offset in the tie order; a
+    wrong shift or a wrong pairing in Eq. (app) changes the offset.  Integer pixels and
+    (r+1)^2 a power of two keep every candidate exact in FP64, so the ties are exact."""
+    H, W = 24, 26
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = alpha * xx + beta * yy + 100.0
+    off = {5: -alpha, 6: alpha, 7: beta, 8: -beta}[win] * r / 2
+    for out in (oracle.fast_filter(img, r, 1, tie=tie)["out"], oracle.filter(img, r, 1, tie=tie)["out"]):
+        inner = (slice(r, H - r), slice(r, W - r))
+        np.testing.assert_array_equal(out[inner], img[inner] + off)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_fast_checkerboard_is_a_fixed_point(r):
+    """Every pixel of a checkerboard with cells of 2r has a quadrant inside its own cell
+    (|d| = 0, and quadrants precede the half windows in the paper order): corners and
+    edges are preserved (the property Sec. 'Fast Approximation' keeps from the exact
+    filter)."""
+    c = 2 * r
+    yy, xx = np.mgrid[0:5 * c, 0:4 * c]
+    img = (((yy // c) + (xx // c)) % 2).astype(np.float64)
+    np.testing.assert_array_equal(oracle.fast_filter(img, r, 4)["out"], img)
+
+
+def test_fast_trivial_cases():
+    img = np.random.default_rng(3).random((5, 6))
+    np.testing.assert_array_equal(oracle.fast_filter(img, 0, 3)["out"], img)   # every window is the pixel
+    np.testing.assert_array_equal(oracle.fast_filter(img, 2, 0)["out"], img)   # no pass
+    flat = np.full((6, 5), 0.375)
+    np.testing.assert_array_equal(oracle.fast_filter(flat, 2, 3)["out"], flat)
