@@ -291,6 +291,26 @@ def form_precision(dev):
     return res
 
 
+def form_fast(dev, x):
+    """The fast approximation (Algorithm 3, Eq. (app)) on the headline workload (4096^2 x 3,
+    r = 8, 30 passes): its throughput next to the exact filter's, and how far its output
+    is from the exact filter's (the comparison the paper plots for the fast variant)."""
+    import torch
+
+    from paper_2108_05021_gb300 import osbf
+
+    r, it = R_, ITERS_
+    o_exact, o_fast = torch.empty_like(x), torch.empty_like(x)
+    t_exact = _time(lambda: osbf.filter(x, r, it, out=o_exact), 10)
+    t_fast = _time(lambda: osbf.filter_fast(x, r, it, out=o_fast), 10)
+    d = (o_fast - o_exact).abs()
+    units = x.numel() * it
+    return {"workload": f"1x3x4096x4096 float32, r={r}, {it} passes", "fast_mpix_iter_s": units / t_fast / 1e6,
+            "exact_mpix_iter_s": units / t_exact / 1e6, "fast_time_over_exact": t_fast / t_exact,
+            "mean_abs_diff_vs_exact": float(d.mean()), "max_abs_diff_vs_exact": float(d.max()),
+            "pixels_differing_from_exact": float((d > 0).float().mean())}
+
+
 def form_sweep(dev, x):
     import torch
 
@@ -400,7 +420,8 @@ def main():
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"fwd_bwd": form_fwd_bwd(dev), "batched": form_batched(dev), "precision": form_precision(dev),
-                 "sweep_4096x3_30_passes": form_sweep(dev, x), "plain_mpix_iter_s": value}
+                 "fast_approximation": form_fast(dev, x), "sweep_4096x3_30_passes": form_sweep(dev, x),
+                 "plain_mpix_iter_s": value}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

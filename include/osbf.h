@@ -115,6 +115,22 @@ osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, in
                              osbf_dtype dtype, void *stream);
 
 /*
+ * The fast approximation of Sec. "Fast Approximation to One-sided Box Filter"
+ * (Algorithm 3, Eq. (app)), float32, paper tie order, the appendix's boundary.  Per
+ * pass one quadrant-mean field (window N1's mean) gives all four quadrant means by
+ * shifts of r, and each half window is approximated by the mean of its two quadrant
+ * means: N5 ~ (N4+N1)/2, N6 ~ (N3+N2)/2, N7 ~ (N1+N2)/2, N8 ~ (N4+N3)/2; then the
+ * selection and update of Algorithm 2.  Not the one-sided box filter itself: its
+ * results differ from osbf_filter()'s wherever a half window wins.
+ *   in, out   N x C x H x W float32 (device).
+ *   maps      optional, as for osbf_filter_ex() (same layout and alignment).
+ * Returns OSBF_EINVAL for null pointers, N, C, H or W <= 0, r or iters < 0, in and out
+ * overlapping, or unaligned maps; OSBF_EUNSUPPORTED for r > OSBF_MAX_RADIUS.
+ */
+osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, int C, int H, int W, int r,
+                             int iters, uint8_t *maps, void *stream);
+
+/*
  * Backward (vector-Jacobian product) of the float32 forward, with each pixel's
  * selection frozen to the map stored by the forward (the selection is piecewise
  * constant, so this is the exact gradient wherever no |d_i| tie is crossed).

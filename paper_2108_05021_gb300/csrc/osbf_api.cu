@@ -572,6 +572,114 @@ osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, in
     return OSBF_OK;
 }
 
+osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, int C, int H, int W, int r, int iters,
+                             uint8_t *maps, void *stream) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->err.clear();
+    ctx->last_launches = 0;
+    if (!in || !out) return fail(ctx, OSBF_EINVAL, "null image pointer");
+    if (N <= 0 || C <= 0 || H <= 0 || W <= 0) return fail(ctx, OSBF_EINVAL, "N, C, H and W must be positive");
+    if (r < 0 || iters < 0) return fail(ctx, OSBF_EINVAL, "r and iters must be >= 0");
+    if (r > OSBF_MAX_RADIUS) return fail(ctx, OSBF_EUNSUPPORTED, "r = %d exceeds OSBF_MAX_RADIUS = %d", r, OSBF_MAX_RADIUS);
+    if (maps && ((uintptr_t)maps & 15)) return fail(ctx, OSBF_EINVAL, "maps must be 16-byte aligned");
+    const long long P = (long long)N * C;
+    if (P * H * (long long)W > (1LL << 40)) return fail(ctx, OSBF_EUNSUPPORTED, "image too large");
+    const size_t bytes = 4 * (size_t)P * H * W;
+    if (overlaps(in, bytes, out, bytes)) return fail(ctx, OSBF_EINVAL, "in and out overlap");
+    const int FH = H + 2 * r, FW = W + 2 * r, FWp = (FW + 31) / 32 * 32, MP = maps_pitch(FW);
+    const long long map_stride = P * FH * MP;
+    if (maps && iters > 0 && (overlaps(maps, (size_t)map_stride * iters, in, bytes) ||
+                              overlaps(maps, (size_t)map_stride * iters, out, bytes)))
+        return fail(ctx, OSBF_EINVAL, "maps overlap an image");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r == 0 || iters == 0) {
+        OSBF_CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s));
+        ctx->last_launches = 1;
+        if (maps && iters > 0) {  // every candidate equals the pixel: N1, first in the paper order
+            OSBF_CK(launch_fill_u8(maps, 1, map_stride * iters, s));
+            ctx->last_launches += 1;
+        }
+        return OSBF_OK;
+    }
+    const size_t frame_bytes = 4 * (size_t)P * FH * FWp;
+    for (int k = 0; k < 2; ++k) {
+        osbf_status e = ensure(ctx, &ctx->frames[k], &ctx->frame_bytes[k], frame_bytes);
+        if (e) return e;
+    }
+    float *frame[2] = {(float *)ctx->frames[0], (float *)ctx->frames[1]};
+    cudaError_t e = launch_pad_replicate(Storage::F32, in, frame[0], (int)P, H, W, r, FH, FW, FWp, s);
+    if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "pad launch failed: %s", cudaGetErrorString(e));
+    ctx->last_launches += 1;
+    const v2::Layout2 L = v2::make_layout2<float>(r, 1, true);
+    const int shift = (4 - r % 4) % 4;  // tile k starts at column k*TW - shift: the TMA box starts on 16 bytes
+    int occ = occupancy_fwd2_fast(r, maps != nullptr);
+    if (occ < 1) occ = 1;
+    int cur = 0;
+    bool wrote_output = false;
+    for (int pass = 0; pass < iters; ++pass) {
+        // the last pass writes the cropped output from registers when its rows hold 16-byte
+        // aligned 4-vectors; otherwise it writes a frame and the crop follows
+        const bool to_output =
+            pass == iters - 1 && W % 4 == 0 && r % 4 == 0 && ((uintptr_t)out % 16) == 0;
+        CUtensorMap map;
+        if (!encode_frame_map(&map, Storage::F32, frame[cur], FW, FH, (int)P, FWp, L.BX, L.RH0))
+            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame %dx%dx%lld)", FW, FH, P);
+        v2::Fwd2Params p;
+        std::memset(&p, 0, sizeof p);
+        p.H = H;
+        p.W = W;
+        p.FH = FH;
+        p.FW = FW;
+        p.D = 1;
+        p.maps = maps;
+        p.map_pitch = MP;
+        p.map_iter0 = pass;
+        p.map_iter_stride = map_stride;
+        p.map_plane = (long long)FH * MP;
+        p.err = ctx->err_word;
+        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1 + shift) / v2::TW;
+        if (to_output) {
+            p.dst = out;
+            p.dst_is_output = 1;
+            p.dst_plane = (long long)H * W;
+            p.dst_pitch = W;
+            if (!maps) {  // with maps, every frame pixel's selection is recorded
+                ty0 = r / v2::TH;
+                ty1 = (r + H - 1) / v2::TH;
+                tx0 = (r + shift) / v2::TW;
+                tx1 = (r + W - 1 + shift) / v2::TW;
+            }
+        } else {
+            p.dst = frame[1 - cur];
+            p.dst_plane = (long long)FH * FWp;
+            p.dst_pitch = FWp;
+        }
+        p.ty_off = ty0;
+        p.tx_off = tx0;
+        p.tx_shift = shift;
+        p.tiles_x = tx1 - tx0 + 1;
+        p.tiles_y = ty1 - ty0 + 1;
+        const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
+        if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
+        p.ntiles = (int)ntiles;
+        const long long gmax = (long long)occ * ctx->sms;
+        e = launch_fwd2_fast(r, maps != nullptr, map, p, (int)(gmax < ntiles ? gmax : ntiles), s);
+        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "fast forward launch failed: %s", cudaGetErrorString(e));
+        ctx->last_launches += 1;
+        if (to_output)
+            wrote_output = true;
+        else
+            cur = 1 - cur;
+    }
+    if (!wrote_output) {
+        e = launch_crop_f32(frame[cur], out, (int)P, H, W, r, FWp, s);
+        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "crop launch failed: %s", cudaGetErrorString(e));
+        ctx->last_launches += 1;
+    }
+    return OSBF_OK;
+}
+
 osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps, int N,
                                  int C, int H, int W, int r, int iters, void *stream) {
     if (!ctx) return OSBF_EINVAL;

@@ -164,6 +164,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // storage-type stores of four floats
 template <typename T> __device__ __forceinline__ void cvt_store4(T *p, float4 v);
@@ -283,7 +284,10 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
 // Output of pass H: a float buffer in shared memory (the next fused pass reads it), or
 // -- DIRECT -- four results at a time straight into the destination frame in global
 // memory (storage type T, 16- or 8-byte stores, rows and columns outside the frame skipped).
-template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT>
+// FAST: the fast approximation (Sec. "Fast Approximation to One-sided Box Filter",
+// Eq. (app)) -- the four quadrant sums are the same running sums, the half windows are
+// the mean of two quadrant means, so the pixel row sums and the exact half sums go away.
+template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
 __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, int urow0,
                                         const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
                                         T *__restrict__ gdst, long long gpitch, const Geom2 &g,
@@ -364,34 +368,42 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 for (int i = 1; i <= R; ++i) {
                     al += ra[(k + P - i) % P];
                     bl += rb[(k + P - i) % P];
-                    ul += ru[(k + P - i) % P];
+                    if (!FAST) ul += ru[(k + P - i) % P];
                 }
                 ABL = make_float2(al, bl);
-                UL = ul;
+                if (!FAST) UL = ul;
             } else {
                 const int so = (k + 2 * P - R - 1) % P;  // the value leaving the window
                 ABL = make_float2(ABL.x + (a - ra[so]), ABL.y + (b - rb[so]));
-                UL += u - ru[so];
+                if (!FAST) UL += u - ru[so];
                 ra[k] = a;
                 rb[k] = b;
                 ru[k] = u;
             }
             hab[k] = ABL;
             // N6 at the current column: the right half window of column x = t - R
-            const float n6 = (ABL.x + ABL.y) - UL;
-            h6[k] = n6;
+            const float n6 = FAST ? 0.f : (ABL.x + ABL.y) - UL;
+            if (!FAST) h6[k] = n6;
             if (t >= 2 * R) {
                 const int sl = (k + P - R) % P;  // column x = t - R; (AL, BL) at x+R is current
                 const float2 ABx = hab[sl];      // (AL(x), BL(x)) = (N4, N1)
                 const float ux = ru[sl];
                 const float2 nu = make_float2(-ux, -ux);
-                const float2 sum = add2(ABx, ABL);
-                const float2 s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);  // (N8, N7)
-                const float2 s56 = make_float2(h6[sl], n6);  // N5(x) = N6(x - r) : left half of x
                 const float2 d41 = fma2(ABx, iq2, nu);
                 const float2 d32 = fma2(ABL, iq2, nu);  // (N3, N2) = (AL(x+r), BL(x+r))
-                const float2 d56 = fma2(s56, ih2, nu);
-                const float2 d87 = fma2(s87, ih2, nu);
+                float2 d56, d87;
+                if (FAST) {
+                    // Eq. (app): d5 = (d4 + d1)/2, d6 = (d3 + d2)/2, d8 = (d4 + d3)/2, d7 = (d1 + d2)/2
+                    const float2 h = make_float2(0.5f, 0.5f);
+                    d56 = mul2(add2(make_float2(d41.x, d32.x), make_float2(d41.y, d32.y)), h);
+                    d87 = mul2(add2(d41, d32), h);
+                } else {
+                    const float2 sum = add2(ABx, ABL);
+                    const float2 s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);  // (N8, N7)
+                    const float2 s56 = make_float2(h6[sl], n6);  // N5(x) = N6(x - r) : left half of x
+                    d56 = fma2(s56, ih2, nu);
+                    d87 = fma2(s87, ih2, nu);
+                }
                 float outv;
                 int m;
                 select2<R, TIE_APP, MAPS>(d41, d32, d56, d87, ux, outv, m);
@@ -462,7 +474,7 @@ __device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &
 // DIRECT: one pass per launch whose results (and selections, with MAPS) go from
 // registers straight into the destination (D == 1, halo EX == R); otherwise every pass
 // lands in shared memory and the tile interior is copied out at the end.
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
 __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
@@ -571,7 +583,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
@@ -615,20 +627,20 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
     }
 }
 
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
 cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream) {
     const Layout2 L = make_layout2<T>(R, p.D, DIRECT);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT>;
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, L.bytes, stream>>>(src, p);
     return cudaGetLastError();
 }
 
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT>
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
 int occupancy_fwd2(int D) {
     const Layout2 L = make_layout2<T>(R, D, DIRECT);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT>;
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, L.bytes) != cudaSuccess) return 0;

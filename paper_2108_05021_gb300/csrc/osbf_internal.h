@@ -38,10 +38,18 @@ size_t smem_fwd2_f32(int R, int D, bool direct);
 size_t smem_fwd2_f16(int R, int D, bool direct);
 size_t smem_fwd2_bf16(int R, int D, bool direct);
 
+// the fast approximation, single pass per launch (float32, paper tie order)
+cudaError_t launch_fwd2_fast(int R, bool maps, const CUtensorMap &src, const v2::Fwd2Params &p, int grid,
+                             cudaStream_t s);
+int occupancy_fwd2_fast(int R, bool maps);
+
 bool encode_frame_map(CUtensorMap *map, Storage st, const void *base, int FW, int FH, int P, int pitch, int box_w,
                       int box_h);
 cudaError_t launch_pad_replicate(Storage st, const void *in, void *frame, int P, int H, int W, int R, int FH, int FW,
                                  int FWp, cudaStream_t s);
+
+// the final crop of a float32 frame into H x W planes (osbf_misc.cu)
+cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W, int R, int FWp, cudaStream_t s);
 
 // elementwise helpers (osbf_misc.cu)
 cudaError_t launch_u8_to_f32(const uint8_t *in, float *out, long long n, cudaStream_t s);
