@@ -286,6 +286,11 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
                                           ((uintptr_t)out % (st == Storage::F32 ? 16 : 8)) == 0);
         const bool direct = Dg == 1 && tie == 0 && out_ok && (st == Storage::F32 || r % 8 == 0);
+        // float32 single passes at r % 4 == 0 (no maps) from frame to frame: results leave
+        // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
+        // stores (the last pass, into the cropped output, keeps the register stores and
+        // the same tile grid, so every call path shares one summation order)
+        const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !maps && !last_out;
         const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
                               : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
                                                    : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
@@ -338,14 +343,18 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         p.tx_shift = shift;
         p.tiles_x = tx1 - tx0 + 1;
         p.tiles_y = ty1 - ty0 + 1;
+        CUtensorMap dmap;
+        if (tstore && !encode_store_map(&dmap, p.dst, FW, FH, P, p.dst_pitch))
+            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame store map)");
         const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
         if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
         p.ntiles = (int)ntiles;
-        int occ = occupancy_v2(st, r, tie != 0, maps != nullptr, direct, Dg);
+        int occ = tstore ? occupancy_fwd2_tstore(r, false) : occupancy_v2(st, r, tie != 0, maps != nullptr, direct, Dg);
         if (occ < 1) occ = 1;
         const long long g = (long long)occ * ctx->sms;
         const int grid = (int)(g < ntiles ? g : ntiles);
-        cudaError_t e = launch_v2(st, r, tie != 0, maps != nullptr, direct, map, p, grid, s);
+        cudaError_t e = tstore ? launch_fwd2_tstore(r, false, map, dmap, p, grid, s)
+                               : launch_v2(st, r, tie != 0, maps != nullptr, direct, map, p, grid, s);
         if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "forward launch failed: %s", cudaGetErrorString(e));
         ctx->last_launches += 1;
         passes += Dg;
@@ -613,8 +622,12 @@ osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, 
     ctx->last_launches += 1;
     const v2::Layout2 L = v2::make_layout2<float>(r, 1, true);
     const int shift = (4 - r % 4) % 4;  // tile k starts at column k*TW - shift: the TMA box starts on 16 bytes
+    // r % 4 == 0 without maps: frame-to-frame passes store through per-warp tensor stores
+    const bool tstore_ok = r % 4 == 0 && !maps;
+    int occ_ts = tstore_ok ? occupancy_fwd2_tstore(r, true) : 0;
     int occ = occupancy_fwd2_fast(r, maps != nullptr);
     if (occ < 1) occ = 1;
+    if (occ_ts < 1) occ_ts = 1;
     int cur = 0;
     bool wrote_output = false;
     for (int pass = 0; pass < iters; ++pass) {
@@ -660,11 +673,17 @@ osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, 
         p.tx_shift = shift;
         p.tiles_x = tx1 - tx0 + 1;
         p.tiles_y = ty1 - ty0 + 1;
+        const bool tstore = tstore_ok && !to_output;
+        CUtensorMap dmap;
+        if (tstore && !encode_store_map(&dmap, frame[1 - cur], FW, FH, (int)P, FWp))
+            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame store map)");
         const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
         if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
         p.ntiles = (int)ntiles;
-        const long long gmax = (long long)occ * ctx->sms;
-        e = launch_fwd2_fast(r, maps != nullptr, map, p, (int)(gmax < ntiles ? gmax : ntiles), s);
+        const long long gmax = (long long)(tstore ? occ_ts : occ) * ctx->sms;
+        const int grid = (int)(gmax < ntiles ? gmax : ntiles);
+        e = tstore ? launch_fwd2_tstore(r, true, map, dmap, p, grid, s)
+                   : launch_fwd2_fast(r, maps != nullptr, map, p, grid, s);
         if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "fast forward launch failed: %s", cudaGetErrorString(e));
         ctx->last_launches += 1;
         if (to_output)

@@ -39,6 +39,7 @@ struct Layout2 {
     int P2;      // float row pitch of the column-sum field A
     int in_bytes;  // bytes of one TMA box
     int off_in, off_uf, off_ab, off_ua, off_ub, bytes;  // byte offsets (128-aligned)
+    int off_st;  // tensor-store staging: NT/32 buffers of 32 x 32 floats, placed 1024-aligned at run time
 };
 
 __host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
@@ -46,7 +47,7 @@ __host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
 // direct: a single pass whose results go straight from registers to the destination
 // frame (no U^1 buffer in shared memory)
 template <typename T>
-__host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false) {
+__host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false, bool tstore = false) {
     Layout2 L;
     const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
     L.EY = D * R;
@@ -77,6 +78,8 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     if (!direct) off = align128(off + rh1 * L.PU * 4);
     L.off_ub = off;
     if (D >= 2) off = align128(off + rh1 * L.PU * 4);
+    L.off_st = off;
+    if (tstore) off = align128(off + 1024 + (NT / 32) * 32 * 32 * 4);  // + slack to reach a 1024-byte boundary
     L.bytes = off + 16;  // + mbarrier
     return L;
 }
@@ -95,6 +98,7 @@ struct Fwd2Params {
     int tiles_x, tiles_y, ntiles;  // tile grid; ntiles = tiles_x * tiles_y * planes
     int ty_off, tx_off;
     int tx_shift;                  // tiles start at column k * TW - tx_shift (direct float32: (4 - R % 4) % 4)
+    int ty_shift;                  // tiles start at row k * TH - ty_shift
     unsigned int *err;         // device error word (bit 0: a bounded wait gave up)
 };
 
@@ -130,6 +134,18 @@ __device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap *map, int x
                  "r"(x), "r"(y), "r"(z)
                  : "memory");
 }
+
+// Tensor store of a shared-memory box (bulk-group completion), and its waits.  The waits
+// are hardware waits on this thread's own copies, not spin loops.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -257,6 +273,7 @@ struct Geom2 {
     int iy0, iy1, ix0, ix1;
     int oy, ox, ly, lx;  // DIRECT destination: frame offset of its origin and its extent
     int MP;              // map row pitch (bytes)
+    int sx0, sy0, sz, sw, sh;  // TSTORE: destination coordinates of the tile's first output, plane, extent
 };
 
 template <int R, bool TIE_APP, bool IDX>
@@ -287,11 +304,17 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
 // FAST: the fast approximation (Sec. "Fast Approximation to One-sided Box Filter",
 // Eq. (app)) -- the four quadrant sums are the same running sums, the half windows are
 // the mean of two quadrant means, so the pixel row sums and the exact half sums go away.
-template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
+// TSTORE (DIRECT float32, R % 4 == 0): each warp stages its 32 x 32 segment in a
+// 1024-aligned shared buffer with the 128-byte swizzle (16-byte chunk c of row y at chunk
+// c ^ (y & 7): the row-owner 4-vectors hit 8 distinct chunks per 8 lanes) and one lane
+// writes it with a tensor store -- the copy engine writes whole lines instead of 32
+// scattered 16-byte pieces per store instruction.
+template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
 __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, int urow0,
                                         const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
                                         T *__restrict__ gdst, long long gpitch, const Geom2 &g,
-                                        uint8_t *__restrict__ mplane) {
+                                        uint8_t *__restrict__ mplane, float *__restrict__ sbase = nullptr,
+                                        const CUtensorMap *dmap = nullptr) {
     constexpr int P = R + 1;         // ring period (the sweep is fully unrolled, so any period is static)
     constexpr int NS = SW + 2 * R;   // sweep steps of one segment (2R of warm-up)
     constexpr int SH = (DIRECT && sizeof(T) == 4) ? (4 - R % 4) % 4 : 0;  // tile grid shift
@@ -304,6 +327,11 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
     for (int item = warp; item < nrb * nseg; item += NT / 32) {
         const int rbk = item % nrb, seg = item / nrb;
         const int yo = rbk * 32 + lane;
+        float *sbuf = TSTORE ? sbase + warp * 32 * 32 : nullptr;
+        if (TSTORE) {
+            if (lane == 0) bulk_wait_read_all();  // the previous tensor store has read this buffer
+            __syncwarp();
+        }
         const bool row_ok = yo < g.RHo;
         const int yr = row_ok ? yo : g.RHo - 1;
         const int xs = seg * SW;
@@ -430,7 +458,10 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                     }
                 } else if (slot == 3) {
                     const float4 v = make_float4(o[0], o[1], o[2], o[3]);
-                    if (DIRECT) {
+                    if (TSTORE) {
+                        const int c = (oo - 3) >> 2;  // 16-byte chunk of the staged row
+                        *reinterpret_cast<float4 *>(sbuf + lane * 32 + ((c ^ (lane & 7)) << 2)) = v;
+                    } else if (DIRECT) {
                         const int dx = g.fx0 - g.ox + xo - 3;  // first column of the 4-vector
                         if (row_store && (unsigned)dx < (unsigned)g.lx) cvt_store4<T>(grow + (oo - 3), v);
                         if (MAPS) {
@@ -444,6 +475,17 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                         orow[oo >> 2] = v;
                     }
                 }
+            }
+        }
+        if (TSTORE) {
+            // every lane's staged writes become visible to the copy engine, then one lane
+            // stores the segment (rows and columns past the destination are clipped by it)
+            fence_proxy_async();
+            __syncwarp();
+            const int x = g.sx0 + xs, y = g.sy0 + rbk * 32;
+            if (lane == 0 && x < g.sw && y < g.sh) {
+                tma_store_3d(dmap, smem_u32(sbuf), x, y, g.sz);
+                bulk_commit();
             }
         }
     }
@@ -467,18 +509,25 @@ __device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &
     const int per = p.tiles_x * p.tiles_y;
     plane = tile / per;
     const int rem = tile - plane * per;
-    ty0 = (rem / p.tiles_x + p.ty_off) * TH;
+    ty0 = (rem / p.tiles_x + p.ty_off) * TH - p.ty_shift;
     tx0 = (rem % p.tiles_x + p.tx_off) * TW - p.tx_shift;
 }
 
 // DIRECT: one pass per launch whose results (and selections, with MAPS) go from
 // registers straight into the destination (D == 1, halo EX == R); otherwise every pass
 // lands in shared memory and the tile interior is copied out at the end.
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
-__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) osbf_fwd2(const __grid_constant__ CUtensorMap src, const Fwd2Params p) {
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 : 3) : 2)
+    osbf_fwd2(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dmap, const Fwd2Params p) {
+    static_assert(!TSTORE || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0), "tensor stores: float32, R % 4 == 0");
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
-    const Layout2 L = make_layout2<T>(R, D, DIRECT);
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE);
+    float *sbase = nullptr;  // TSTORE staging, 1024-aligned (the 128-byte swizzle repeats every 1024 bytes)
+    if (TSTORE) {
+        const uint32_t a = smem_u32(smem2 + L.off_st);
+        sbase = reinterpret_cast<float *>(smem2 + L.off_st + (((a + 1023u) & ~1023u) - a));
+    }
     T *bin = reinterpret_cast<T *>(smem2 + L.off_in);
     float *uf = reinterpret_cast<float *>(smem2 + (sizeof(T) == 4 ? L.off_in : L.off_uf));
     float *A = reinterpret_cast<float *>(smem2 + L.off_ab);
@@ -533,6 +582,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
                 atomicOr(p.err, 1u);
                 mbar_wait_bounded(bar, phase);
             }
+            if (TSTORE && (threadIdx.x & 31) == 0) bulk_wait_all();
             return;
         }
         phase ^= 1;
@@ -579,11 +629,19 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
             g.ly = p.dst_is_output ? p.H : p.FH;
             g.lx = p.dst_is_output ? p.W : p.FW;
             g.MP = p.map_pitch;
+            if (TSTORE) {  // destination coordinates of the tile's first output column / row
+                g.sx0 = g.fx0 - g.ox;
+                g.sy0 = g.fy0 - g.oy;
+                g.sz = plane;
+                g.sw = g.lx;
+                g.sh = g.ly;
+            }
             uint8_t *mplane = nullptr;
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane);
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g,
+                                                               mplane, sbase, &dmap);
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
@@ -625,22 +683,25 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS ? 4 : 3) : 2) os
         }
         __syncthreads();
     }
+    if (TSTORE && (threadIdx.x & 31) == 0) bulk_wait_all();  // this warp's last segment store is complete
 }
 
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
-cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream) {
-    const Layout2 L = make_layout2<T>(R, p.D, DIRECT);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST>;
+// dmap: the destination's tensor map (read only by TSTORE kernels; any map otherwise)
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
+cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream,
+                        const CUtensorMap *dmap = nullptr) {
+    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NT, L.bytes, stream>>>(src, p);
+    kern<<<grid, NT, L.bytes, stream>>>(src, dmap ? *dmap : src, p);
     return cudaGetLastError();
 }
 
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false>
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
 int occupancy_fwd2(int D) {
-    const Layout2 L = make_layout2<T>(R, D, DIRECT);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST>;
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, L.bytes) != cudaSuccess) return 0;

@@ -43,6 +43,15 @@ cudaError_t launch_fwd2_fast(int R, bool maps, const CUtensorMap &src, const v2:
                              cudaStream_t s);
 int occupancy_fwd2_fast(int R, bool maps);
 
+// single-pass float32 launches with per-warp tensor stores (R % 4 == 0, paper tie order, no maps)
+cudaError_t launch_fwd2_tstore(int R, bool fast, const CUtensorMap &src, const CUtensorMap &dmap,
+                               const v2::Fwd2Params &p, int grid, cudaStream_t s);
+int occupancy_fwd2_tstore(int R, bool fast);
+
+// A float32 destination for tensor stores: P planes of H rows x W elements (row pitch
+// `pitch` elements), 32 x 32 boxes staged with the 128-byte swizzle.
+bool encode_store_map(CUtensorMap *map, void *base, int W, int H, int P, int pitch);
+
 bool encode_frame_map(CUtensorMap *map, Storage st, const void *base, int FW, int FH, int P, int pitch, int box_w,
                       int box_h);
 cudaError_t launch_pad_replicate(Storage st, const void *in, void *frame, int P, int H, int W, int R, int FH, int FW,
