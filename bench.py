@@ -49,7 +49,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one forward launch of the headline workload, from one ncu
 # capture of that launch (to be reset to None whenever the kernel changes)
-TRAFFIC_PER_LAUNCH = 359.0e6
+TRAFFIC_PER_LAUNCH = 364.5e6
 
 
 def hbm_peak():
@@ -390,16 +390,35 @@ def main():
     value = whole_job_rate(pix_iters, ws, ms_step * 1e-3) / 1e6
 
     # roofline of the forward tile kernel: every launch reads and writes each frame pixel
-    # once (the replicate-pad launch is one of the step's launches and is cheaper)
+    # once.  Its average launch duration is measured live with CUDA events on the launching
+    # stream: a 30-pass call and a 2-pass call differ by exactly 28 frame-to-frame launches
+    # of that kernel (both share the pad launch and the final launch into the output).
     FH, FW = H_ + 2 * r, W_ + 2 * r
     bytes_per_launch = 8.0 * N_ * C_ * FH * FW
-    launch_ms = ms_step / max(launches_per_step, 1)
+    nrep = max(3, min(20, args.steps // 10))
+
+    def timed(iters_):
+        for _ in range(2):
+            osbf.filter(x, r, iters_, depth=args.depth, out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nrep):
+            osbf.filter(x, r, iters_, depth=args.depth, out=out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / nrep
+
+    if ITERS_ > 2:
+        launch_ms = (timed(ITERS_) - timed(2)) / (ITERS_ - 2)
+    else:
+        launch_ms = ms_step / max(launches_per_step, 1)
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_LAUNCH if r == R_ and args.depth in (0, 1) else None,
-                "peak_source": peak_kind, "kernel": "osbf_fwd2 (forward tile kernel)",
+                "peak_source": peak_kind, "kernel": "osbf_fwd2 (forward tile kernel, frame to frame, tensor stores)",
                 "bytes_per_launch": bytes_per_launch, "launches_per_step": launches_per_step,
+                "launch_ms": launch_ms, "launch_ms_method": "CUDA events: (30-pass call - 2-pass call) / 28",
                 "hbm_roofline_equiv_mpix_iter_s": peak * 1e9 / 8.0 / 1e6}
 
     e2e = None
