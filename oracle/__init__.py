@@ -2,7 +2,8 @@
 
 A plain, slow, FP64 (int64 for 8-bit input) implementation of Algorithm 2 with
 the appendix's boundary rule, by direct summation over each one-sided window
-(Eq. (6)-(13)), and of the fast approximation (Algorithm 3, Eq. (app)).  Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
+(Eq. (6)-(13)), of the fast approximation (Algorithm 3, Eq. (app)), and of the 3D
+filter (Sec. "Higher Dimension Case").  Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may use it; the CUDA library never imports it and shares no
 code with it.  The arithmetic lives in ``osbf_oracle.c``; this module only
 builds that file with gcc and marshals numpy arrays into it.
@@ -63,6 +64,8 @@ def _load():
         lib.oracle_filter_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, vp, d, vp, i]
         lib.oracle_fast_filter_f64.restype = i
         lib.oracle_fast_filter_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, vp, d, vp]
+        lib.oracle_filter3d_f64.restype = i
+        lib.oracle_filter3d_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, d, vp]
         lib.oracle_filter_region_f64.restype = i
         lib.oracle_filter_region_f64.argtypes = [vp, i, i, i, i, i, i, i, i, i, vp, vp, i, d, vp]
         lib.oracle_u8_first_pass.restype = i
@@ -186,6 +189,27 @@ def fast_filter(x: np.ndarray, r: int, iters: int, tie: str = "paper", want_maps
     _check(_load().oracle_fast_filter_f64(_ptr(x3), _ptr(out), P, H, W, r, iters, TIE[tie], _ptr(maps), _ptr(gaps),
                                           _ptr(h), float(hint_thresh), ctypes.addressof(nh)))
     return {"out": out.reshape(shape), "maps": maps, "gaps": gaps, "n_hinted": int(nh.value)}
+
+
+def filter3d(x: np.ndarray, r: int, iters: int, want_maps: bool = False, hint: Optional[np.ndarray] = None,
+             hint_thresh: float = 1e-6):
+    """The 3D filter (Sec. "Higher Dimension Case") on D x H x W, P x D x H x W or
+    N x C x D x H x W input: pad every axis by r, `iters` passes over 14 windows, crop.
+    Returns {"out", "maps" (iters x P x FD x FH x FW, window 1..14), "n_hinted"}."""
+    a = np.asarray(x)
+    shape = a.shape
+    x4 = np.ascontiguousarray(a.reshape((-1,) + shape[-3:]), dtype=np.float64)
+    P, D, H, W = x4.shape
+    FD, FH, FW = D + 2 * r, H + 2 * r, W + 2 * r
+    out = np.empty_like(x4)
+    maps = np.zeros((iters, P, FD, FH, FW), dtype=np.uint8) if (want_maps or hint is not None) else None
+    h = None
+    if hint is not None:
+        h = np.ascontiguousarray(hint, dtype=np.uint8).reshape(iters, P, FD, FH, FW)
+    nh = ctypes.c_longlong(0)
+    _check(_load().oracle_filter3d_f64(_ptr(x4), _ptr(out), P, D, H, W, r, iters, _ptr(maps), _ptr(h),
+                                       float(hint_thresh), ctypes.addressof(nh)))
+    return {"out": out.reshape(shape), "maps": maps, "n_hinted": int(nh.value)}
 
 
 def filter_region(plane: np.ndarray, r: int, iters: int, y0: int, y1: int, x0: int, x1: int,

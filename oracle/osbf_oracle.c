@@ -24,6 +24,9 @@
  *     (Algorithm 3, Eq. (app)): one quadrant-mean field per pass, the other three
  *     quadrants read from it at shifts of r, the four half windows approximated by
  *     the mean of their two quadrant means (oracle_fast_iterate_frame_f64).
+ *   - the higher-dimension case of Sec. "Higher Dimension Case" in 3D: eight corner
+ *     (octant) windows of (r+1)^3 voxels and six half windows of (r+1)(2r+1)^2 voxels,
+ *     the same selection and update (oracle_filter3d_f64).
  * Readings of the paper taken here (the paper is silent or self-inconsistent):
  *   - `iters` passes (the appendix's `for it = 1:ItNum`), not IterationNum+1;
  *   - tie order "paper": N1..N8; tie order "appendix": the appendix's difference
@@ -34,7 +37,13 @@
  *     (0, +r), (-r, 0), (-r, +r) in (row, column); N5 ~ (a4 + a1)/2, N6 ~ (a3 + a2)/2,
  *     N7 ~ (a1 + a2)/2 (the paper's example), N8 ~ (a4 + a3)/2; selection, update,
  *     tie orders and boundary as in Algorithm 2 (the garbled argmin and update lines of
- *     Algorithm 3 read this way).
+ *     Algorithm 3 read this way);
+ *   - 3D: the paper gives no listing and no window order.  Boundary as in 2D (replicate
+ *     pad by r once, zeros beyond the padded volume, crop).  Window order: octants O1..O4
+ *     = depth z-r..z with the 2D quadrants N1..N4 in (y, x), O5..O8 = depth z..z+r with
+ *     N1..N4, then the halves H9 = x-r..x, H10 = x..x+r (full y, z), H11 = y..y+r,
+ *     H12 = y-r..y (full x, z), H13 = z-r..z, H14 = z..z+r (full x, y); ties go to the
+ *     first window in that order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -554,4 +563,121 @@ int oracle_adjoint_f64(const double *grad_out, const uint8_t *maps, double *grad
     free(g);
     free(gn);
     return ORACLE_OK;
+}
+
+/*
+ * The 3D one-sided box filter (Sec. "Higher Dimension Case"), `iters` passes on P padded
+ * volumes of FD x FH x FW (frames, FP64, updated in place).  Window w = 1..14: offsets
+ * [z0,z1] x [y0,y1] x [x0,x1] from the table in window3d(); sums by direct summation with
+ * zeros outside the volume; means with the fixed window sizes; first argmin |mean - U|
+ * in window order; U' = the chosen mean (Jacobi).  maps / hint as in 2D (14 windows).
+ */
+static void window3d(int w, int r, int *z0, int *z1, int *y0, int *y1, int *x0, int *x1) {
+    /* the 2D quadrants N1..N4 in (y, x): N1 y..y+r, x-r..x; N2 y..y+r, x..x+r;
+       N3 y-r..y, x..x+r; N4 y-r..y, x-r..x */
+    static const int qy[4][2] = {{0, 1}, {0, 1}, {-1, 0}, {-1, 0}};
+    static const int qx[4][2] = {{-1, 0}, {0, 1}, {0, 1}, {-1, 0}};
+    if (w <= 8) {
+        int q = (w - 1) % 4;
+        *z0 = w <= 4 ? -r : 0;
+        *z1 = w <= 4 ? 0 : r;
+        *y0 = qy[q][0] * r;
+        *y1 = qy[q][1] * r;
+        *x0 = qx[q][0] * r;
+        *x1 = qx[q][1] * r;
+        return;
+    }
+    *z0 = -r; *z1 = r; *y0 = -r; *y1 = r; *x0 = -r; *x1 = r;
+    switch (w) {
+    case 9: *x1 = 0; break;   /* left  */
+    case 10: *x0 = 0; break;  /* right */
+    case 11: *y0 = 0; break;  /* down (rows y..y+r) */
+    case 12: *y1 = 0; break;  /* up   (rows y-r..y) */
+    case 13: *z1 = 0; break;  /* front (depth z-r..z) */
+    default: *z0 = 0; break;  /* 14: back (depth z..z+r) */
+    }
+}
+
+int oracle_filter3d_iterate_f64(double *frame, int P, int FD, int FH, int FW, int r, int iters, uint8_t *maps,
+                                const uint8_t *hint, double hint_thresh, long long *n_hinted) {
+    if (P <= 0 || FD <= 0 || FH <= 0 || FW <= 0 || r < 0 || iters < 0) return ORACLE_EINVAL;
+    size_t vol = (size_t)FD * FH * FW, total = (size_t)P * vol;
+    double *next = (double *)malloc(sizeof(double) * (total ? total : 1));
+    if (!next) return ORACLE_ENOMEM;
+    long long hinted = 0;
+    for (int t = 0; t < iters; ++t) {
+#pragma omp parallel for schedule(static) reduction(+ : hinted)
+        for (long row = 0; row < (long)P * FD * FH; ++row) {
+            int p = (int)(row / ((long)FD * FH)), z = (int)((row / FH) % FD), y = (int)(row % FH);
+            const double *V = frame + (size_t)p * vol;
+            for (int x = 0; x < FW; ++x) {
+                size_t idx = (size_t)p * vol + ((size_t)z * FH + y) * FW + x;
+                double u = V[((size_t)z * FH + y) * FW + x];
+                double mean[15], ad[15];
+                for (int w = 1; w <= 14; ++w) {
+                    int z0, z1, y0, y1, x0, x1;
+                    window3d(w, r, &z0, &z1, &y0, &y1, &x0, &x1);
+                    double s = 0.0;
+                    for (int zz = z + z0; zz <= z + z1; ++zz) {
+                        if (zz < 0 || zz >= FD) continue;
+                        for (int yy = y + y0; yy <= y + y1; ++yy) {
+                            if (yy < 0 || yy >= FH) continue;
+                            for (int xx = x + x0; xx <= x + x1; ++xx)
+                                if (xx >= 0 && xx < FW) s += V[((size_t)zz * FH + yy) * FW + xx];
+                        }
+                    }
+                    double n = (double)(z1 - z0 + 1) * (double)(y1 - y0 + 1) * (double)(x1 - x0 + 1);
+                    mean[w] = s / n;
+                    ad[w] = fabs(mean[w] - u);
+                }
+                int m = 1;
+                for (int w = 2; w <= 14; ++w)
+                    if (ad[w] < ad[m]) m = w;
+                size_t tidx = (size_t)t * total + idx;
+                if (hint) {
+                    int h = hint[tidx];
+                    if (h >= 1 && h <= 14 && h != m && ad[h] - ad[m] < hint_thresh) {
+                        if (mean[h] != mean[m]) hinted += 1;
+                        m = h;
+                    }
+                }
+                next[idx] = mean[m];
+                if (maps) maps[tidx] = (uint8_t)m;
+            }
+        }
+        memcpy(frame, next, sizeof(double) * total);
+    }
+    free(next);
+    if (n_hinted) *n_hinted = hinted;
+    return ORACLE_OK;
+}
+
+/* The 3D filter on P volumes of D x H x W: replicate pad by r on every axis, iterate, crop. */
+int oracle_filter3d_f64(const double *in, double *out, int P, int D, int H, int W, int r, int iters, uint8_t *maps,
+                        const uint8_t *hint, double hint_thresh, long long *n_hinted) {
+    if (P <= 0 || D <= 0 || H <= 0 || W <= 0 || r < 0 || iters < 0) return ORACLE_EINVAL;
+    int FD = D + 2 * r, FH = H + 2 * r, FW = W + 2 * r;
+    size_t fvol = (size_t)FD * FH * FW;
+    double *frame = (double *)malloc(sizeof(double) * (size_t)P * fvol);
+    if (!frame) return ORACLE_ENOMEM;
+    for (int p = 0; p < P; ++p)
+        for (int z = 0; z < FD; ++z)
+            for (int y = 0; y < FH; ++y)
+                for (int x = 0; x < FW; ++x) {
+                    int sz = z - r < 0 ? 0 : (z - r >= D ? D - 1 : z - r);
+                    int sy = y - r < 0 ? 0 : (y - r >= H ? H - 1 : y - r);
+                    int sx = x - r < 0 ? 0 : (x - r >= W ? W - 1 : x - r);
+                    frame[(size_t)p * fvol + ((size_t)z * FH + y) * FW + x] =
+                        in[(((size_t)p * D + sz) * H + sy) * W + sx];
+                }
+    int st = oracle_filter3d_iterate_f64(frame, P, FD, FH, FW, r, iters, maps, hint, hint_thresh, n_hinted);
+    if (st == ORACLE_OK)
+        for (int p = 0; p < P; ++p)
+            for (int z = 0; z < D; ++z)
+                for (int y = 0; y < H; ++y)
+                    for (int x = 0; x < W; ++x)
+                        out[(((size_t)p * D + z) * H + y) * W + x] =
+                            frame[(size_t)p * fvol + ((size_t)(z + r) * FH + y + r) * FW + x + r];
+    free(frame);
+    return st;
 }

@@ -483,3 +483,92 @@ def test_fast_trivial_cases():
     np.testing.assert_array_equal(oracle.fast_filter(img, 2, 0)["out"], img)   # no pass
     flat = np.full((6, 5), 0.375)
     np.testing.assert_array_equal(oracle.fast_filter(flat, 2, 3)["out"], flat)
+
+
+# ---------------------------------------------------------------------------------
+# The 3D filter (Sec. "Higher Dimension Case"): eight octants, six half windows.
+# ---------------------------------------------------------------------------------
+def _windows3d(r):
+    """Windows as explicit voxel-offset sets: O1..O4 = depth -r..0 with the 2D quadrants
+    N1..N4 in (y, x), O5..O8 = depth 0..r with N1..N4, then the halves x-, x+, y+, y-, z-,
+    z+ (full span on the other two axes)."""
+    neg, pos, full = range(-r, 1), range(0, r + 1), range(-r, r + 1)
+    quads = [(pos, neg), (pos, pos), (neg, pos), (neg, neg)]  # (y, x) of N1..N4
+    wins = [(zs, ys, xs) for zs in (neg, pos) for (ys, xs) in quads]
+    wins += [(full, full, neg), (full, full, pos), (full, pos, full), (full, neg, full), (neg, full, full),
+             (pos, full, full)]
+    return [[(dz, dy, dx) for dz in zs for dy in ys for dx in xs] for (zs, ys, xs) in wins]
+
+
+def _filter3d_brute(vol, r, iters):
+    D, H, W = vol.shape
+    FD, FH, FW = D + 2 * r, H + 2 * r, W + 2 * r
+    V = np.empty((FD, FH, FW))
+    for z in range(FD):
+        for y in range(FH):
+            for x in range(FW):
+                V[z, y, x] = vol[min(max(z - r, 0), D - 1), min(max(y - r, 0), H - 1), min(max(x - r, 0), W - 1)]
+    wins = _windows3d(r)
+    for _ in range(iters):
+        nxt = np.empty_like(V)
+        for z in range(FD):
+            for y in range(FH):
+                for x in range(FW):
+                    best, bm = None, None
+                    for offs in wins:
+                        s = 0.0
+                        for dz, dy, dx in offs:
+                            zz, yy, xx = z + dz, y + dy, x + dx
+                            if 0 <= zz < FD and 0 <= yy < FH and 0 <= xx < FW:
+                                s += V[zz, yy, xx]
+                        m = s / len(offs)
+                        if best is None or abs(m - V[z, y, x]) < best:
+                            best, bm = abs(m - V[z, y, x]), m
+                    nxt[z, y, x] = bm
+        V = nxt
+    return V[r:r + D, r:r + H, r:r + W]
+
+
+@pytest.mark.parametrize("r,iters", [(1, 1), (1, 2), (2, 1)])
+def test_filter3d_matches_brute_force(r, iters):
+    vol = np.random.default_rng(7 + r + iters).random((3, 4, 5))
+    np.testing.assert_allclose(oracle.filter3d(vol, r, iters)["out"], _filter3d_brute(vol, r, iters), rtol=0,
+                               atol=1e-12)
+
+
+@pytest.mark.parametrize("abc,off", [
+    ((1, 2, 4), -1),   # octant offsets r/2 (+-1 +-2 +-4): O2 (z-, y+, x+) is the first with |.| = 1
+    ((4, 2, 1), +1),   # O3 (z-, y-, x+): +4 -2 -1
+    ((1, 8, 16), -1),  # octants >= 7, halves 1 / 8 / 16: H9 (x-) first
+    ((16, 1, 8), +1),  # H11 (y+)
+    ((8, 16, 1), -1),  # H13 (z-)
+    # exact opposite-sign ties between octants: only the window order decides
+    ((3, 1, 3), +1),   # O2 (z-, y+, x+) = +1 before O3 (z-, y-, x+) = -1
+    ((3, 3, 1), -1),   # O1 (z-, y+, x-) = -1 before O5 (z+, y+, x-) = +1: the z- octants come first
+    ((1, 3, 3), -1),   # O1 (z-, y+, x-) = -1 before O2 (z-, y+, x+) = +1
+])
+def test_filter3d_linear_ramp_closed_form(abc, off):
+    """On U = a x + b y + c z an octant mean is U + r/2 (+-a +-b +-c) and a half window's
+    U +- r/2 times one coefficient; interior voxels move by the first smallest offset in
+    the window order.  Integers with r = 1 keep every mean exact in FP64 ((r+1)^3 = 8; the
+    half-window quotients are correctly rounded), so the ties are exact.  The five cases
+    pin the octant signs, the half windows and the order."""
+    a, b, c = abc
+    r, D, H, W = 1, 6, 7, 8
+    zz, yy, xx = np.mgrid[0:D, 0:H, 0:W].astype(np.float64)
+    vol = a * xx + b * yy + c * zz + 200.0
+    out = oracle.filter3d(vol, r, 1)["out"]
+    inner = (slice(r, D - r), slice(r, H - r), slice(r, W - r))
+    np.testing.assert_array_equal(out[inner], vol[inner] + off * r / 2)
+
+
+def test_filter3d_fixed_points():
+    flat = np.full((5, 6, 7), 0.625)
+    np.testing.assert_array_equal(oracle.filter3d(flat, 2, 3)["out"], flat)
+    r, c = 1, 2
+    zz, yy, xx = np.mgrid[0:4 * c, 0:3 * c, 0:5 * c]
+    cb = (((zz // c) + (yy // c) + (xx // c)) % 2).astype(np.float64)   # every voxel owns an octant of its cell
+    np.testing.assert_array_equal(oracle.filter3d(cb, r, 3)["out"], cb)
+    vol = np.random.default_rng(1).random((3, 4, 5))
+    np.testing.assert_array_equal(oracle.filter3d(vol, 0, 2)["out"], vol)
+    np.testing.assert_array_equal(oracle.filter3d(vol, 2, 0)["out"], vol)
