@@ -311,6 +311,29 @@ def form_fast(dev, x):
             "pixels_differing_from_exact": float((d > 0).float().mean())}
 
 
+def form_volume(dev):
+    """The 3D filter (Sec. "Higher Dimension Case"): 1 x 1 x 128 x 256 x 256 float32 volume,
+    r = 2 (the radius of the paper's volume example), 10 passes."""
+    import torch
+
+    from paper_2108_05021_gb300 import osbf, synth
+
+    D, H, W, r, it = 128, 256, 256, 2, 10
+    scenes = synth.piecewise_stack(1, 4, H, W, seed=11, sigma=0.0)[0]
+    rng = np.random.default_rng(11)
+    vol = np.concatenate([np.repeat(scenes[k][None], D // 4, axis=0) for k in range(4)])
+    vol = np.clip(vol + rng.normal(0, 0.05, vol.shape), 0, 1).astype(np.float32)[None, None]
+    x = torch.from_numpy(vol).to(dev)
+    out = torch.empty_like(x)
+    t = _time(lambda: osbf.filter3d(x, r, it, out=out), 10)
+    units = D * H * W * it
+    FD, FH, FW = D + 2 * r, H + 2 * r, W + 2 * r
+    return {"workload": f"1x1x{D}x{H}x{W} float32, r={r}, {it} passes", "gvox_iter_s": units / t / 1e9,
+            "ms_per_call": t * 1e3,
+            # per pass: z-pass reads U, writes Zm, Zp; yx-pass reads U, Zm, Zp and writes U'
+            "bytes_per_pass_algorithmic_min": 8 * FD * FH * FW, "bytes_per_pass_two_kernels": 28 * FD * FH * FW}
+
+
 def form_sweep(dev, x):
     import torch
 
@@ -439,7 +462,8 @@ def main():
     forms = None
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"fwd_bwd": form_fwd_bwd(dev), "batched": form_batched(dev), "precision": form_precision(dev),
-                 "fast_approximation": form_fast(dev, x), "sweep_4096x3_30_passes": form_sweep(dev, x),
+                 "fast_approximation": form_fast(dev, x), "volume_3d": form_volume(dev),
+                 "sweep_4096x3_30_passes": form_sweep(dev, x),
                  "plain_mpix_iter_s": value}
 
     cpu = None

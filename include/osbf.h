@@ -130,6 +130,29 @@ osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, in
 osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, int C, int H, int W, int r,
                              int iters, uint8_t *maps, void *stream);
 
+/* Largest radius of the 3D filter. */
+#define OSBF_MAX_RADIUS_3D 4
+
+/*
+ * The 3D one-sided box filter of Sec. "Higher Dimension Case": per voxel the eight
+ * corner (octant) windows of (r+1)^3 voxels and the six half windows of (r+1)(2r+1)^2
+ * voxels (left/right, down/up, front/back: half along one axis, full along the other
+ * two), mean of each, first argmin |mean - U| in the order O1..O8, H9..H14 below, U <-
+ * that mean; `iters` passes; volumes replicate-padded by r on every axis once, zeros
+ * beyond the padded volume, cropped at the end (the appendix's 2D boundary, extended).
+ * Window order: O1..O4 = depth z-r..z with the quadrants N1..N4 of Eq. (6)-(9) in (y, x),
+ * O5..O8 = depth z..z+r with N1..N4, H9 = x-r..x, H10 = x..x+r, H11 = y..y+r, H12 =
+ * y-r..y, H13 = z-r..z, H14 = z..z+r.  Float32.
+ *   in, out   N x C x D x H x W (device).
+ *   maps      optional, iters x N*C x (D+2r) x (H+2r) x (W+2r) bytes: window 1..14 per
+ *             padded voxel and pass.
+ * Returns OSBF_EINVAL for null pointers, non-positive sizes, r or iters < 0, in and out
+ * overlapping; OSBF_EUNSUPPORTED for r > OSBF_MAX_RADIUS_3D or volumes whose padded
+ * height exceeds 65535 or N*C*(D+2r) exceeds 65535.
+ */
+osbf_status osbf_filter_3d(osbf_ctx *ctx, const float *in, float *out, int N, int C, int D, int H, int W, int r,
+                           int iters, uint8_t *maps, void *stream);
+
 /*
  * Backward (vector-Jacobian product) of the float32 forward, with each pixel's
  * selection frozen to the map stored by the forward (the selection is piecewise

@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
         L.osbf_filter_ex.restype = st
         L.osbf_filter_fast.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
         L.osbf_filter_fast.restype = st
+        L.osbf_filter_3d.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, vp, vp]
+        L.osbf_filter_3d.restype = st
         L.osbf_filter_host.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, vp]
         L.osbf_filter_host.restype = st
         L.osbf_filter_backward.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
@@ -223,6 +225,36 @@ def filter_fast(x: torch.Tensor, r: int, iters: int, *, maps: Optional[torch.Ten
     dev = x.device.index
     ctx = context(dev)
     _check(lib().osbf_filter_fast(ctx, x.data_ptr(), out.data_ptr(), N, C, H, W, r, iters, mp, _stream(dev)), ctx)
+    return out
+
+
+def maps3d_shape(x: torch.Tensor, r: int, iters: int):
+    """Shape of the 3D filter's selection maps: (iters, N*C, D+2r, H+2r, W+2r)."""
+    N, C, D, H, W = x.shape
+    return (iters, N * C, D + 2 * r, H + 2 * r, W + 2 * r)
+
+
+def filter3d(x: torch.Tensor, r: int, iters: int, *, maps: Optional[torch.Tensor] = None,
+             out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """The 3D filter (osbf_filter_3d; Sec. "Higher Dimension Case") on float32 N x C x D x H x W."""
+    _require_cuda(x)
+    if x.dim() != 5 or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("filter3d takes a contiguous float32 N x C x D x H x W tensor")
+    N, C, D, H, W = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    _require_cuda(out)
+    if out.dtype != torch.float32 or out.shape != x.shape:
+        raise ValueError("out has the wrong dtype or shape")
+    mp = None
+    if maps is not None:
+        _require_cuda(maps)
+        if maps.dtype != torch.uint8 or tuple(maps.shape) != maps3d_shape(x, r, iters):
+            raise ValueError(f"maps must be uint8 of shape {maps3d_shape(x, r, iters)}")
+        mp = maps.data_ptr()
+    dev = x.device.index
+    ctx = context(dev)
+    _check(lib().osbf_filter_3d(ctx, x.data_ptr(), out.data_ptr(), N, C, D, H, W, r, iters, mp, _stream(dev)), ctx)
     return out
 
 
