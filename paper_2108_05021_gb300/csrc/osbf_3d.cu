@@ -17,7 +17,8 @@
 //              H11 / H12 = Xf(Y+(Zf)) / Xf(Y-(Zf)),  Xf(X) = L(x) + L(x+r) - X(x);
 //              H13 / H14 = Xf(Yf(Zm)) / Xf(Yf(Zp)).
 // Window sums are re-formed from their register rings at every step (r <= 4), so no
-// running sum drifts.
+// running sum drifts.  The yx-pass tile regions arrive by TMA (the tile grid is shifted by
+// (4 - r % 4) % 4 columns so every box starts on 16 bytes).
 #include <cstring>
 
 #include "osbf.h"
@@ -27,6 +28,7 @@ osbf_status osbf_ctx_fail(osbf_ctx *ctx, osbf_status code, const char *msg);
 void *osbf_ctx_workspace(osbf_ctx *ctx, int slot, size_t bytes, osbf_status *st);
 void osbf_ctx_count_launches(osbf_ctx *ctx, int n);
 void osbf_ctx_reset_launches(osbf_ctx *ctx);
+unsigned int *osbf_ctx_err_word(osbf_ctx *ctx);
 
 namespace osbf {
 namespace v3 {
@@ -84,87 +86,123 @@ __global__ void zpass_kernel(const float *__restrict__ U, float *__restrict__ Zm
 }
 
 struct YXParams {
-    const float *U, *Zm, *Zp;  // frames (current pass)
-    float *dst;                 // next frame, or the cropped output (dst_is_output)
+    float *dst;          // next frame, or the cropped output (dst_is_output)
     int dst_is_output;
-    uint8_t *maps;              // this pass's maps (P x FD x FH x FW) or null
+    uint8_t *maps;       // this pass's maps (P x FD x FH x FW) or null
     Vol v;
     int tiles_x, tiles_y;
+    int shift;           // tile k starts at frame column k * TW - shift: the boxes start on 16 bytes
+    unsigned int *err;   // bit 0: a tile load did not land in time
 };
 
-__host__ __device__ constexpr int pitch3(int R) {
-    // row pitch of the shared fields: the region width TW + 2R, made odd so that the
-    // row-owner scalar loads of pass H (32 lanes on 32 rows) hit 32 distinct banks
-    return TW + 2 * R + 1;
+// Width (floats) of the TMA boxes, also the row pitch of every shared field: the region
+// TW + 2R plus pass H's float4 over-read, a multiple of 4 (16-byte rows) with
+// pitch % 8 == 4, so the row-owner float4 loads of pass H are conflict-free.
+__host__ __device__ constexpr int bx3(int R) {
+    return ((TW + 2 * R + 4 + 3) / 4 * 4) % 8 == 4 ? (TW + 2 * R + 4 + 3) / 4 * 4 : (TW + 2 * R + 4 + 3) / 4 * 4 + 4;
 }
+__host__ __device__ constexpr int align128_3(int b) { return (b + 127) & ~127; }
+// byte offsets: three boxes, three up-sum fields, the mbarrier
+__host__ __device__ constexpr int box_bytes3(int R) { return (TH + 2 * R) * bx3(R) * 4; }
+__host__ __device__ constexpr int off_a3(int R) { return 3 * align128_3(box_bytes3(R)); }
+__host__ __device__ constexpr int smem3(int R) { return off_a3(R) + 3 * align128_3((TH + R) * bx3(R) * 4) + 16; }
 
-template <int R>
-__global__ void __launch_bounds__(NT) yx_kernel(const YXParams q) {
-    constexpr int RH = TH + 2 * R, RW = TW + 2 * R, PU = pitch3(R);
+// One CTA per (slice, 32 x 64 tile): the tile's region of U, Zm and Zp arrives by three
+// TMA copies (zeros outside the frame), pass V forms the up-column sums, pass H selects.
+template <int R, bool MAPS>
+__global__ void __launch_bounds__(NT) yx_kernel(const __grid_constant__ CUtensorMap mU,
+                                                const __grid_constant__ CUtensorMap mM,
+                                                const __grid_constant__ CUtensorMap mP, const YXParams q) {
+    constexpr int RH = TH + 2 * R, RW = TW + 2 * R, BX = bx3(R);
     constexpr int P = R + 1;
     constexpr float io = 1.0f / float((R + 1) * (R + 1) * (R + 1));
     constexpr float ih = 1.0f / float((R + 1) * (2 * R + 1) * (2 * R + 1));
-    extern __shared__ __align__(16) float sm3[];
-    float *bU = sm3, *bM = bU + RH * PU, *bP = bM + RH * PU;                      // input boxes
-    float *aU = bP + RH * PU, *aM = aU + (RH - R) * PU, *aP = aM + (RH - R) * PU;  // up-column sums
+    extern __shared__ __align__(128) unsigned char sm3[];
+    float *bU = reinterpret_cast<float *>(sm3), *bM = reinterpret_cast<float *>(sm3 + align128_3(box_bytes3(R))),
+          *bP = reinterpret_cast<float *>(sm3 + 2 * align128_3(box_bytes3(R)));
+    constexpr int ab = align128_3((TH + R) * BX * 4);
+    float *aU = reinterpret_cast<float *>(sm3 + off_a3(R)), *aM = reinterpret_cast<float *>(sm3 + off_a3(R) + ab),
+          *aP = reinterpret_cast<float *>(sm3 + off_a3(R) + 2 * ab);
+    const uint32_t bar = v2::smem_u32(sm3 + smem3(R) - 16);
     const Vol &v = q.v;
     const int tile = blockIdx.x, zp = blockIdx.y;
     const int z = zp % v.FD, p = zp / v.FD;
-    const int ty0 = (tile / q.tiles_x) * TH, tx0 = (tile % q.tiles_x) * TW;
+    const int ty0 = (tile / q.tiles_x) * TH, tx0 = (tile % q.tiles_x) * TW - q.shift;
     const long long slice = (long long)p * v.fplane + (long long)z * v.FH * v.FWp;
 
-    // region (TH + 2R) x (TW + 2R) of U, Zm, Zp in this slice; zero outside the frame
-    for (int e = threadIdx.x; e < RH * RW; e += NT) {
-        const int y = e / RW, x = e - y * RW;
-        const int fy = ty0 - R + y, fx = tx0 - R + x;
-        float u = 0.f, m = 0.f, pp = 0.f;
-        if ((unsigned)fy < (unsigned)v.FH && (unsigned)fx < (unsigned)v.FW) {
-            const long long o = slice + (long long)fy * v.FWp + fx;
-            u = q.U[o];
-            m = q.Zm[o];
-            pp = q.Zp[o];
-        }
-        bU[y * PU + x] = u;
-        bM[y * PU + x] = m;
-        bP[y * PU + x] = pp;
+    if (threadIdx.x == 0) {
+        v2::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        v2::fence_proxy_async();
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(3 * box_bytes3(R))
+                     : "memory");
+        const CUtensorMap *maps3[3] = {&mU, &mM, &mP};
+        float *dst3[3] = {bU, bM, bP};
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                "%3, %4}], [%5];" ::"r"(v2::smem_u32(dst3[f])),
+                "l"(reinterpret_cast<uint64_t>(maps3[f])), "r"(tx0 - R), "r"(ty0 - R), "r"(zp), "r"(bar)
+                : "memory");
     }
     __syncthreads();
+    const bool timed_out = !v2::mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(timed_out)) {
+        if (threadIdx.x == 0) {
+            atomicOr(q.err, 1u);
+            v2::mbar_wait_bounded(bar, 0);  // let late copies land before the CTA leaves
+        }
+        return;
+    }
 
-    // pass V: up-column sums (rows s-R..s) of the three fields, stored at row s - R
-    for (int c = threadIdx.x; c < RW; c += NT) {
-        float ru[P], rm[P], rp[P];
+    // pass V: up-column sums (rows s-R..s) of the three fields, stored at row s - R; one
+    // thread per column pair
+    for (int c2 = threadIdx.x; 2 * c2 < RW; c2 += NT) {
+        const int c = 2 * c2;
+        float2 ru[P], rm[P], rp[P];
 #pragma unroll
-        for (int k = 0; k < P; ++k) ru[k] = rm[k] = rp[k] = 0.f;
+        for (int k = 0; k < P; ++k) ru[k] = rm[k] = rp[k] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int s = 0; s < RH; ++s) {
             const int k = s % P;
-            ru[k] = bU[s * PU + c];
-            rm[k] = bM[s * PU + c];
-            rp[k] = bP[s * PU + c];
+            ru[k] = *reinterpret_cast<const float2 *>(bU + s * BX + c);
+            rm[k] = *reinterpret_cast<const float2 *>(bM + s * BX + c);
+            rp[k] = *reinterpret_cast<const float2 *>(bP + s * BX + c);
             if (s >= R) {
-                float su = ru[0], smm = rm[0], spp = rp[0];
+                float2 su = ru[0], smm = rm[0], spp = rp[0];
 #pragma unroll
                 for (int i = 1; i < P; ++i) {
-                    su += ru[i];
-                    smm += rm[i];
-                    spp += rp[i];
+                    su = __fadd2_rn(su, ru[i]);
+                    smm = __fadd2_rn(smm, rm[i]);
+                    spp = __fadd2_rn(spp, rp[i]);
                 }
-                aU[(s - R) * PU + c] = su;
-                aM[(s - R) * PU + c] = smm;
-                aP[(s - R) * PU + c] = spp;
+                *reinterpret_cast<float2 *>(aU + (s - R) * BX + c) = su;
+                *reinterpret_cast<float2 *>(aM + (s - R) * BX + c) = smm;
+                *reinterpret_cast<float2 *>(aP + (s - R) * BX + c) = spp;
             }
         }
     }
     __syncthreads();
 
-    // pass H: lane = output row, warp = 32-column segment
+    // pass H: lane = output row, warp = 32-column segment; shared loads as float4 groups
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int y = lane, xs = warp * SW;
     constexpr int NS = SW + 2 * R;
+    const float4 *gau = reinterpret_cast<const float4 *>(aU + y * BX + xs);
+    const float4 *gbu = reinterpret_cast<const float4 *>(aU + (y + R) * BX + xs);
+    const float4 *gam = reinterpret_cast<const float4 *>(aM + y * BX + xs);
+    const float4 *gbm = reinterpret_cast<const float4 *>(aM + (y + R) * BX + xs);
+    const float4 *gap = reinterpret_cast<const float4 *>(aP + y * BX + xs);
+    const float4 *gbp = reinterpret_cast<const float4 *>(aP + (y + R) * BX + xs);
+    const float4 *gcu = reinterpret_cast<const float4 *>(bU + (y + R) * BX + xs);
+    const float4 *gcm = reinterpret_cast<const float4 *>(bM + (y + R) * BX + xs);
+    const float4 *gcp = reinterpret_cast<const float4 *>(bP + (y + R) * BX + xs);
+    float4 vau, vbu, vam, vbm, vap, vbp, vcu, vcm, vcp;
     // nine row fields, by step t (region column xs + t): 0 Y-(Zm) 1 Y+(Zm) 2 Y-(Zp) 3 Y+(Zp)
     // 4 Yf(Zf) 5 Y+(Zf) 6 Y-(Zf) 7 Yf(Zm) 8 Yf(Zp)
-    float rf[9][P];   // field values of the last P columns
-    float lh[9][P];   // their left sums L at the last P columns
+    float rf[9][P];  // field values of the last P columns
+    float lh[9][P];  // their left sums L at the last P columns
 #pragma unroll
     for (int f = 0; f < 9; ++f)
 #pragma unroll
@@ -173,12 +211,22 @@ __global__ void __launch_bounds__(NT) yx_kernel(const YXParams q) {
     const int fy = ty0 + y;
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
-        const int k = t % P;
-        const int c = xs + t;
-        const float amu = aU[y * PU + c], bpu = aU[(y + R) * PU + c];
-        const float amm = aM[y * PU + c], bpm = aM[(y + R) * PU + c];
-        const float amp = aP[y * PU + c], bpp = aP[(y + R) * PU + c];
-        const float uc = bU[(y + R) * PU + c], mc = bM[(y + R) * PU + c], pc = bP[(y + R) * PU + c];
+        const int k = t % P, j = t & 3;
+        if (j == 0) {
+            const int g = t >> 2;
+            vau = gau[g];
+            vbu = gbu[g];
+            vam = gam[g];
+            vbm = gbm[g];
+            vap = gap[g];
+            vbp = gbp[g];
+            vcu = gcu[g];
+            vcm = gcm[g];
+            vcp = gcp[g];
+        }
+        const float amu = f4get(vau, j), bpu = f4get(vbu, j), amm = f4get(vam, j), bpm = f4get(vbm, j);
+        const float amp = f4get(vap, j), bpp = f4get(vbp, j);
+        const float uc = f4get(vcu, j), mc = f4get(vcm, j), pc = f4get(vcp, j);
         const float zf = mc + pc - uc;
         const float ymzf = amm + amp - amu, ypzf = bpm + bpp - bpu;
         float fv[9];
@@ -195,10 +243,10 @@ __global__ void __launch_bounds__(NT) yx_kernel(const YXParams q) {
 #pragma unroll
         for (int f = 0; f < 9; ++f) {
             rf[f][k] = fv[f];
-            float s = fv[f];
+            float sum = fv[f];
 #pragma unroll
-            for (int i = 1; i < P; ++i) s += rf[f][(k + P - i) % P];
-            lh[f][k] = s;  // L at column t (valid once t >= R)
+            for (int i = 1; i < P; ++i) sum += rf[f][(k + P - i) % P];
+            lh[f][k] = sum;  // L at column t (valid once t >= R)
         }
         if (t >= 2 * R) {
             const int sl = (k + P - R) % P;  // column x = t - R: the output pixel's column
@@ -212,23 +260,34 @@ __global__ void __launch_bounds__(NT) yx_kernel(const YXParams q) {
             mean[6] = lh[3][k] * io;
             mean[7] = lh[2][k] * io;
             mean[8] = lh[2][sl] * io;
-            mean[9] = lh[4][sl] * ih;                                 // H9: x-
-            mean[10] = lh[4][k] * ih;                                 // H10: x+
-            mean[11] = (lh[5][sl] + lh[5][k] - rf[5][sl]) * ih;       // H11: y+
-            mean[12] = (lh[6][sl] + lh[6][k] - rf[6][sl]) * ih;       // H12: y-
-            mean[13] = (lh[7][sl] + lh[7][k] - rf[7][sl]) * ih;       // H13: z-
-            mean[14] = (lh[8][sl] + lh[8][k] - rf[8][sl]) * ih;       // H14: z+
-            float best = mean[1] - u;
-            int m = 1;
+            mean[9] = lh[4][sl] * ih;                            // H9: x-
+            mean[10] = lh[4][k] * ih;                            // H10: x+
+            mean[11] = (lh[5][sl] + lh[5][k] - rf[5][sl]) * ih;  // H11: y+
+            mean[12] = (lh[6][sl] + lh[6][k] - rf[6][sl]) * ih;  // H12: y-
+            mean[13] = (lh[7][sl] + lh[7][k] - rf[7][sl]) * ih;  // H13: z-
+            mean[14] = (lh[8][sl] + lh[8][k] - rf[8][sl]) * ih;  // H14: z+
+            // first argmin |mean_w - u| as a tournament: in every pick the left operand
+            // holds the earlier windows and keeps ties, so the first index still wins
+            float d[15];
+            int id[15];
 #pragma unroll
-            for (int w = 2; w <= 14; ++w) {
-                const float d = mean[w] - u;
-                const bool take = fabsf(d) < fabsf(best);
-                best = take ? d : best;
-                m = take ? w : m;
+            for (int w = 1; w <= 14; ++w) {
+                d[w] = mean[w] - u;
+                id[w] = w;
             }
+            auto pick = [&](int a, int b) {  // into slot a
+                const bool take = fabsf(d[b]) < fabsf(d[a]);
+                d[a] = take ? d[b] : d[a];
+                if (MAPS) id[a] = take ? id[b] : id[a];
+            };
+            pick(1, 2); pick(3, 4); pick(5, 6); pick(7, 8); pick(9, 10); pick(11, 12); pick(13, 14);
+            pick(1, 3); pick(5, 7); pick(9, 11);
+            pick(1, 5); pick(9, 13);
+            pick(1, 9);
+            const float best = d[1];
+            const int m = id[1];
             const int fx = tx0 + xs + t - 2 * R;
-            if (fy < v.FH && fx < v.FW) {
+            if (fy < v.FH && (unsigned)fx < (unsigned)v.FW) {
                 const float outv = u + best;
                 if (q.dst_is_output) {
                     const int oz = z - R, oy = fy - R, ox = fx - R;
@@ -237,20 +296,20 @@ __global__ void __launch_bounds__(NT) yx_kernel(const YXParams q) {
                 } else {
                     q.dst[slice + (long long)fy * v.FWp + fx] = outv;
                 }
-                if (q.maps)
-                    q.maps[(((long long)p * v.FD + z) * v.FH + fy) * v.FW + fx] = (uint8_t)m;
+                if (MAPS) q.maps[(((long long)p * v.FD + z) * v.FH + fy) * v.FW + fx] = (uint8_t)m;
             }
         }
     }
 }
 
 template <int R>
-cudaError_t launch_yx(const YXParams &q, int nslices, cudaStream_t s) {
-    constexpr int RH = TH + 2 * R, PU = pitch3(R);
-    const size_t bytes = sizeof(float) * (size_t)(3 * RH * PU + 3 * (RH - R) * PU);
-    cudaError_t e = cudaFuncSetAttribute(yx_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t launch_yx(const CUtensorMap &mU, const CUtensorMap &mM, const CUtensorMap &mP, const YXParams &q,
+                      int nslices, cudaStream_t s) {
+    const int bytes = smem3(R);
+    auto kern = q.maps ? yx_kernel<R, true> : yx_kernel<R, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    yx_kernel<R><<<dim3(q.tiles_x * q.tiles_y, nslices), NT, bytes, s>>>(q);
+    kern<<<dim3(q.tiles_x * q.tiles_y, nslices), NT, bytes, s>>>(mU, mM, mP, q);
     return cudaGetLastError();
 }
 
@@ -327,22 +386,28 @@ extern "C" osbf_status osbf_filter_3d(osbf_ctx *ctx, const float *in, float *out
         if (e != cudaSuccess) return osbf_ctx_fail(ctx, OSBF_ECUDA, cudaGetErrorString(e));
         v3::YXParams q;
         std::memset(&q, 0, sizeof q);
-        q.U = fr[cur];
-        q.Zm = Zm;
-        q.Zp = Zp;
         const bool last = pass == iters - 1;
         q.dst = last ? out : fr[1 - cur];
         q.dst_is_output = last ? 1 : 0;
         q.maps = maps ? maps + pass * mstride : nullptr;
         q.v = v;
-        q.tiles_x = (v.FW + v3::TW - 1) / v3::TW;
+        q.shift = (4 - r % 4) % 4;
+        q.tiles_x = (v.FW - 1 + q.shift) / v3::TW + 1;
         q.tiles_y = (v.FH + v3::TH - 1) / v3::TH;
+        q.err = osbf_ctx_err_word(ctx);
         const int nslices = (int)(P * v.FD);
+        // the three fields as P*FD slices of FH x FW (row pitch FWp); boxes of the tile region
+        const int bx = r == 1 ? v3::bx3(1) : r == 2 ? v3::bx3(2) : r == 3 ? v3::bx3(3) : v3::bx3(4);
+        CUtensorMap mU, mM, mP;
+        if (!encode_frame_map(&mU, Storage::F32, fr[cur], v.FW, v.FH, nslices, v.FWp, bx, v3::TH + 2 * r) ||
+            !encode_frame_map(&mM, Storage::F32, Zm, v.FW, v.FH, nslices, v.FWp, bx, v3::TH + 2 * r) ||
+            !encode_frame_map(&mP, Storage::F32, Zp, v.FW, v.FH, nslices, v.FWp, bx, v3::TH + 2 * r))
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (3D fields)");
         switch (r) {
-        case 1: e = v3::launch_yx<1>(q, nslices, s); break;
-        case 2: e = v3::launch_yx<2>(q, nslices, s); break;
-        case 3: e = v3::launch_yx<3>(q, nslices, s); break;
-        case 4: e = v3::launch_yx<4>(q, nslices, s); break;
+        case 1: e = v3::launch_yx<1>(mU, mM, mP, q, nslices, s); break;
+        case 2: e = v3::launch_yx<2>(mU, mM, mP, q, nslices, s); break;
+        case 3: e = v3::launch_yx<3>(mU, mM, mP, q, nslices, s); break;
+        case 4: e = v3::launch_yx<4>(mU, mM, mP, q, nslices, s); break;
         }
         if (e != cudaSuccess) return osbf_ctx_fail(ctx, OSBF_ECUDA, cudaGetErrorString(e));
         osbf_ctx_count_launches(ctx, 2);
