@@ -2,8 +2,9 @@
 
 A plain, slow, FP64 (int64 for 8-bit input) implementation of Algorithm 2 with
 the appendix's boundary rule, by direct summation over each one-sided window
-(Eq. (6)-(13)), of the fast approximation (Algorithm 3, Eq. (app)), and of the 3D
-filter (Sec. "Higher Dimension Case").  Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
+(Eq. (6)-(13)), of the fast approximation (Algorithm 3, Eq. (app)), of the 3D
+filter (Sec. "Higher Dimension Case"), and of the one-sided Gaussian filter
+(Algorithm 1 with the kernels of Sec. "Separable Kernels").  Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may use it; the CUDA library never imports it and shares no
 code with it.  The arithmetic lives in ``osbf_oracle.c``; this module only
 builds that file with gcc and marshals numpy arrays into it.
@@ -66,6 +67,8 @@ def _load():
         lib.oracle_fast_filter_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, vp, d, vp]
         lib.oracle_filter3d_f64.restype = i
         lib.oracle_filter3d_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, d, vp]
+        lib.oracle_gauss_filter_f64.restype = i
+        lib.oracle_gauss_filter_f64.argtypes = [vp, vp, i, i, i, i, i, i, d, vp, vp, d, vp]
         lib.oracle_filter_region_f64.restype = i
         lib.oracle_filter_region_f64.argtypes = [vp, i, i, i, i, i, i, i, i, i, vp, vp, i, d, vp]
         lib.oracle_u8_first_pass.restype = i
@@ -209,6 +212,25 @@ def filter3d(x: np.ndarray, r: int, iters: int, want_maps: bool = False, hint: O
     nh = ctypes.c_longlong(0)
     _check(_load().oracle_filter3d_f64(_ptr(x4), _ptr(out), P, D, H, W, r, iters, _ptr(maps), _ptr(h),
                                        float(hint_thresh), ctypes.addressof(nh)))
+    return {"out": out.reshape(shape), "maps": maps, "n_hinted": int(nh.value)}
+
+
+def gauss_filter(x: np.ndarray, r: int, iters: int, sigma: float, tie: str = "paper", want_maps: bool = False,
+                 hint: Optional[np.ndarray] = None, hint_thresh: float = 1e-6):
+    """The one-sided Gaussian filter (Algorithm 1, Phi = weighted mean with the kernels of
+    Sec. "Separable Kernels"): pad, `iters` passes, crop.  Same shapes and dict as filter()."""
+    shape = np.asarray(x).shape
+    x3 = np.ascontiguousarray(_planes(x), dtype=np.float64)
+    P, H, W = x3.shape
+    FH, FW = H + 2 * r, W + 2 * r
+    out = np.empty_like(x3)
+    maps = np.zeros((iters, P, FH, FW), dtype=np.uint8) if (want_maps or hint is not None) else None
+    h = None
+    if hint is not None:
+        h = np.ascontiguousarray(hint, dtype=np.uint8).reshape(iters, P, FH, FW)
+    nh = ctypes.c_longlong(0)
+    _check(_load().oracle_gauss_filter_f64(_ptr(x3), _ptr(out), P, H, W, r, iters, TIE[tie], float(sigma), _ptr(maps),
+                                           _ptr(h), float(hint_thresh), ctypes.addressof(nh)))
     return {"out": out.reshape(shape), "maps": maps, "n_hinted": int(nh.value)}
 
 

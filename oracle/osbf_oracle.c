@@ -27,6 +27,9 @@
  *   - the higher-dimension case of Sec. "Higher Dimension Case" in 3D: eight corner
  *     (octant) windows of (r+1)^3 voxels and six half windows of (r+1)(2r+1)^2 voxels,
  *     the same selection and update (oracle_filter3d_f64).
+ *   - the one-sided Gaussian filter (Algorithm 1 with Phi = a weighted mean, Sec.
+ *     "Separable Kernels", Eq. (oneside)): the eight windows weighted by products of
+ *     normalised one-sided and full 1D Gaussian kernels (oracle_gauss_filter_f64).
  * Readings of the paper taken here (the paper is silent or self-inconsistent):
  *   - `iters` passes (the appendix's `for it = 1:ItNum`), not IterationNum+1;
  *   - tie order "paper": N1..N8; tie order "appendix": the appendix's difference
@@ -43,7 +46,14 @@
  *     = depth z-r..z with the 2D quadrants N1..N4 in (y, x), O5..O8 = depth z..z+r with
  *     N1..N4, then the halves H9 = x-r..x, H10 = x..x+r (full y, z), H11 = y..y+r,
  *     H12 = y-r..y (full x, z), H13 = z-r..z, H14 = z..z+r (full x, y); ties go to the
- *     first window in that order.
+ *     first window in that order;
+ *   - one-sided Gaussian: k(u) = exp(-u^2 / (2 sigma^2)) on -r..r; both one-sided kernels
+ *     include the centre tap (Eq. (oneside) writes u > 0 for the right half; the box
+ *     kernels and the 3D kernels include u = 0 on both sides, and with it sigma -> inf
+ *     gives the one-sided box filter); each 1D kernel is normalised over its own taps,
+ *     each 2D window kernel is the product of its two 1D kernels (quadrants: one-sided x
+ *     one-sided; halves: one-sided x full); the appendix's boundary (zeros outside the
+ *     padded frame, weights not renormalised there).
  */
 #include <math.h>
 #include <stdint.h>
@@ -678,6 +688,105 @@ int oracle_filter3d_f64(const double *in, double *out, int P, int D, int H, int 
                     for (int x = 0; x < W; ++x)
                         out[(((size_t)p * D + z) * H + y) * W + x] =
                             frame[(size_t)p * fvol + ((size_t)(z + r) * FH + y + r) * FW + x + r];
+    free(frame);
+    return st;
+}
+
+/*
+ * One-sided Gaussian filter (Algorithm 1 with Phi = the weighted mean of Sec. "Separable
+ * Kernels"), `iters` passes on padded frames, in place.  wh[k], k = 0..r: the one-sided
+ * 1D kernel (distance k from the centre); wf[k], k = 0..r: the full 1D kernel at offset
+ * +-k.  Window i's kernel is wy(dy) * wx(dx) over its offsets (Eq. (6)-(13)), with wy / wx
+ * = wh on a one-sided axis and wf on a full axis.  Selection and update as Algorithm 2.
+ */
+int oracle_gauss_iterate_frame_f64(double *frame, int P, int FH, int FW, int r, int iters, int tie,
+                                   double sigma, uint8_t *maps, const uint8_t *hint, double hint_thresh,
+                                   long long *n_hinted) {
+    if (P <= 0 || FH <= 0 || FW <= 0 || r < 0 || iters < 0 || tie < 0 || tie > 1 || !(sigma > 0))
+        return ORACLE_EINVAL;
+    double *g = (double *)malloc(sizeof(double) * (r + 1));
+    double *wh = (double *)malloc(sizeof(double) * (r + 1));
+    double *wf = (double *)malloc(sizeof(double) * (r + 1));
+    size_t plane = (size_t)FH * FW, total = (size_t)P * plane;
+    double *next = (double *)malloc(sizeof(double) * (total ? total : 1));
+    if (!g || !wh || !wf || !next) {
+        free(g); free(wh); free(wf); free(next);
+        return ORACLE_ENOMEM;
+    }
+    double sh = 0.0, sf = 0.0;
+    for (int k = 0; k <= r; ++k) {
+        g[k] = exp(-(double)k * k / (2.0 * sigma * sigma));
+        sh += g[k];
+        sf += k == 0 ? g[k] : 2.0 * g[k];
+    }
+    for (int k = 0; k <= r; ++k) {
+        wh[k] = g[k] / sh;
+        wf[k] = g[k] / sf;
+    }
+    const int *order = TIE_ORDER[tie];
+    long long hinted = 0;
+    for (int t = 0; t < iters; ++t) {
+#pragma omp parallel for schedule(static) reduction(+ : hinted)
+        for (long row = 0; row < (long)P * FH; ++row) {
+            int p = (int)(row / FH), y = (int)(row % FH);
+            const double *V = frame + (size_t)p * plane;
+            for (int x = 0; x < FW; ++x) {
+                size_t idx = (size_t)p * plane + (size_t)y * FW + x;
+                double u = V[(size_t)y * FW + x];
+                double mean[9], ad[9];
+                for (int i = 1; i <= 8; ++i) {
+                    int dy0, dy1, dx0, dx1;
+                    window_offsets(i, r, &dy0, &dy1, &dx0, &dx1);
+                    const int yfull = dy0 == -r && dy1 == r, xfull = dx0 == -r && dx1 == r;
+                    double s = 0.0;
+                    for (int dy = dy0; dy <= dy1; ++dy) {
+                        int yy = y + dy;
+                        if (yy < 0 || yy >= FH) continue;
+                        double wy = yfull ? wf[abs(dy)] : wh[abs(dy)];
+                        for (int dx = dx0; dx <= dx1; ++dx) {
+                            int xx = x + dx;
+                            if (xx < 0 || xx >= FW) continue;
+                            double wx = xfull ? wf[abs(dx)] : wh[abs(dx)];
+                            s += wy * wx * V[(size_t)yy * FW + xx];
+                        }
+                    }
+                    mean[i] = s;
+                    ad[i] = fabs(s - u);
+                }
+                int m = order[0];
+                for (int k = 1; k < 8; ++k)
+                    if (ad[order[k]] < ad[m]) m = order[k];
+                size_t tidx = (size_t)t * total + idx;
+                if (hint) {
+                    int h = hint[tidx];
+                    if (h >= 1 && h <= 8 && h != m && ad[h] - ad[m] < hint_thresh) {
+                        if (mean[h] != mean[m]) hinted += 1;
+                        m = h;
+                    }
+                }
+                next[idx] = mean[m];
+                if (maps) maps[tidx] = (uint8_t)m;
+            }
+        }
+        memcpy(frame, next, sizeof(double) * total);
+    }
+    free(g); free(wh); free(wf); free(next);
+    if (n_hinted) *n_hinted = hinted;
+    return ORACLE_OK;
+}
+
+/* The one-sided Gaussian filter on P planes of H x W: pad, iterate, crop. */
+int oracle_gauss_filter_f64(const double *in, double *out, int P, int H, int W, int r, int iters, int tie,
+                            double sigma, uint8_t *maps, const uint8_t *hint, double hint_thresh,
+                            long long *n_hinted) {
+    if (P <= 0 || H <= 0 || W <= 0 || r < 0 || iters < 0) return ORACLE_EINVAL;
+    int FH = H + 2 * r, FW = W + 2 * r;
+    double *frame = (double *)malloc(sizeof(double) * (size_t)P * FH * FW);
+    if (!frame) return ORACLE_ENOMEM;
+    oracle_pad_replicate_f64(in, frame, P, H, W, r);
+    int st = oracle_gauss_iterate_frame_f64(frame, P, FH, FW, r, iters, tie, sigma, maps, hint, hint_thresh,
+                                            n_hinted);
+    if (st == ORACLE_OK) oracle_crop_f64(frame, out, P, H, W, r);
     free(frame);
     return st;
 }

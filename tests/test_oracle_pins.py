@@ -572,3 +572,135 @@ def test_filter3d_fixed_points():
     vol = np.random.default_rng(1).random((3, 4, 5))
     np.testing.assert_array_equal(oracle.filter3d(vol, 0, 2)["out"], vol)
     np.testing.assert_array_equal(oracle.filter3d(vol, 2, 0)["out"], vol)
+
+
+# ----------------------------------------------------------------------------------
+# one-sided Gaussian filter (Algorithm 1, kernels of Sec. "Separable Kernels")
+# ----------------------------------------------------------------------------------
+def gauss_brute_force(img, r, iters, sigma):
+    """Eq. (6)-(13) windows as set predicates; each window's kernel the product of a 1D
+    kernel per axis, one-sided (centre included, normalised over 0..r) on an axis the
+    window halves, full (normalised over -r..r) on an axis it spans; zeros outside the
+    padded frame; first argmin in window order."""
+    import math
+    g = [math.exp(-k * k / (2.0 * sigma * sigma)) for k in range(r + 1)]
+    half, full = sum(g), g[0] + 2 * sum(g[1:])
+    H, W = len(img), len(img[0])
+    FH, FW = H + 2 * r, W + 2 * r
+    U = [[img[min(max(fy - r, 0), H - 1)][min(max(fx - r, 0), W - 1)] for fx in range(FW)] for fy in range(FH)]
+    for _ in range(iters):
+        new = [[0.0] * FW for _ in range(FH)]
+        for y in range(FH):
+            for x in range(FW):
+                best, best_ad = None, None
+                for i in range(1, 9):
+                    # an axis is spanned when the window holds the taps on both sides of the centre
+                    xfull = _in_window(i, r, x, y, x - 1, y) and _in_window(i, r, x, y, x + 1, y)
+                    yfull = _in_window(i, r, x, y, x, y - 1) and _in_window(i, r, x, y, x, y + 1)
+                    s = 0.0
+                    for v in range(y - r, y + r + 1):
+                        for u in range(x - r, x + r + 1):
+                            if 0 <= v < FH and 0 <= u < FW and _in_window(i, r, x, y, u, v):
+                                wy = g[abs(v - y)] / (full if yfull else half)
+                                wx = g[abs(u - x)] / (full if xfull else half)
+                                s += wy * wx * U[v][u]
+                    ad = abs(s - U[y][x])
+                    if best is None or ad < best_ad:
+                        best, best_ad = s, ad
+                new[y][x] = best
+        U = new
+    return np.array([row[r:r + W] for row in U[r:r + H]])
+
+
+@pytest.mark.parametrize("r,iters,sigma", [(1, 1, 0.8), (1, 2, 3.0), (2, 2, 1.7), (3, 1, 1.0)])
+def test_gauss_oracle_matches_brute_force(r, iters, sigma):
+    img = np.random.default_rng(40 + r).random((6, 7))
+    got = oracle.gauss_filter(img, r, iters, sigma)["out"]
+    np.testing.assert_allclose(got, gauss_brute_force(img.tolist(), r, iters, sigma), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("r", [1, 2, 5])
+def test_gauss_large_sigma_is_the_box_filter(r):
+    # sigma = +inf turns every weight flat: the one-sided box filter (Sec. 4 opening)
+    img = synth.piecewise_stack(1, 2, 19, 23, seed=7 + r)[0].astype(np.float64)
+    a = oracle.gauss_filter(img, r, 3, 1e12, want_maps=True)
+    b = oracle.filter(img, r, 3, want_maps=True)
+    np.testing.assert_allclose(a["out"], b["out"], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(a["maps"], b["maps"])
+
+
+def _scipy_kernels(r, sigma):
+    """Full and one-sided 1D kernels taken from scipy's Gaussian: the impulse response of
+    gaussian_filter1d truncated at radius r, and its centre-and-right half renormalised."""
+    e = np.zeros(2 * r + 1)
+    e[r] = 1.0
+    full = ndi.gaussian_filter1d(e, sigma, truncate=r / sigma, mode="constant")   # taps -r..r
+    half = full[r:] / full[r:].sum()                                               # taps 0..r
+    return full, half
+
+
+def _one_sided_1d(s, half, side):
+    # side -1: sum_k half[k] s(x - k); side +1: sum_k half[k] s(x + k); zeros off the ends
+    r = len(half) - 1
+    p = np.concatenate([np.zeros(r), s, np.zeros(r)])
+    n = len(s)
+    return sum(half[k] * p[r + side * k: r + side * k + n] for k in range(r + 1))
+
+
+@pytest.mark.parametrize("r,sigma", [(2, 1.0), (3, 3.0), (5, 1.6)])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_gauss_one_axis_signal_against_scipy(r, sigma, axis):
+    """An image varying along one axis only: away from the frame's ends on the other axis,
+    every window mean is a 1D one-sided (k^-, k^+) or full (k) Gaussian mean of the signal,
+    scipy's gaussian_filter1d for the full one (Eq. (oneside))."""
+    full, half = _scipy_kernels(r, sigma)
+    s = np.random.default_rng(r + 10 * axis).random(17)
+    img = np.tile(s, (12, 1)) if axis == 1 else np.tile(s[:, None], (1, 12))
+    out = oracle.gauss_filter(img, r, 1, sigma)["out"]
+    sp = np.pad(s, r, mode="edge")                     # the frame along the signal's axis
+    cand_lo = _one_sided_1d(sp, half, -1)[r:-r]        # x - r..x (or y - r..y)
+    cand_hi = _one_sided_1d(sp, half, +1)[r:-r]
+    cand_f = ndi.gaussian_filter1d(sp, sigma, truncate=r / sigma, mode="constant")[r:-r]
+    # window order 1..8 along x: lo, hi, hi, lo, lo, hi, full, full; along y: hi, hi, lo,
+    # lo, full, full, hi, lo -- the first argmin is the first of lo / hi / full to win
+    first = [cand_lo, cand_hi, cand_f] if axis == 1 else [cand_hi, cand_lo, cand_f]
+    ad = np.stack([np.abs(c - s) for c in first])
+    exp1d = np.stack(first)[np.argmin(ad, axis=0), np.arange(len(s))]
+    # rows (or columns) whose windows stay inside the frame on the constant axis
+    inner = out[r:12 - r, :] if axis == 1 else out[:, r:12 - r].T
+    for line in inner:
+        np.testing.assert_allclose(line, exp1d, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("r,sigma", [(2, 1.2), (4, 3.0)])
+def test_gauss_additive_image_products(r, sigma):
+    """f(y, x) = a(y) + b(x): with normalised product kernels each window mean splits
+    into a y-mean of a plus an x-mean of b, the halves set by Eq. (6)-(13)."""
+    full, half = _scipy_kernels(r, sigma)
+    rng = np.random.default_rng(5)
+    H, W = 14, 15
+    a, b = rng.random(H), rng.random(W)
+    img = a[:, None] + b[None, :]
+    out = oracle.gauss_filter(img, r, 1, sigma)["out"]
+    ap, bp = np.pad(a, r, mode="edge"), np.pad(b, r, mode="edge")
+    ya = {"lo": _one_sided_1d(ap, half, -1), "hi": _one_sided_1d(ap, half, +1),
+          "f": ndi.gaussian_filter1d(ap, sigma, truncate=r / sigma, mode="constant")}
+    xb = {"lo": _one_sided_1d(bp, half, -1), "hi": _one_sided_1d(bp, half, +1),
+          "f": ndi.gaussian_filter1d(bp, sigma, truncate=r / sigma, mode="constant")}
+    # (y part, x part) of N1..N8, y growing downwards
+    parts = [("hi", "lo"), ("hi", "hi"), ("lo", "hi"), ("lo", "lo"), ("f", "lo"), ("f", "hi"), ("hi", "f"), ("lo", "f")]
+    for y in range(r, H - r):            # frame rows 2r.., windows inside the frame
+        for x in range(r, W - r):
+            fy, fx = y + r, x + r
+            means = [ya[py][fy] + xb[px][fx] for py, px in parts]
+            ad = [abs(m - img[y, x]) for m in means]
+            assert abs(out[y, x] - means[int(np.argmin(ad))]) < 1e-12
+
+
+def test_gauss_constant_interior_and_trivial_cases():
+    flat = np.full((9, 10), 0.375)
+    out = oracle.gauss_filter(flat, 2, 1, 1.3)["out"]
+    np.testing.assert_allclose(out[2:-2, 2:-2], flat[2:-2, 2:-2], rtol=0, atol=1e-15)
+    img = np.random.default_rng(3).random((5, 6))
+    np.testing.assert_array_equal(oracle.gauss_filter(img, 0, 3, 1.0)["out"], img)
+    np.testing.assert_array_equal(oracle.gauss_filter(img, 2, 0, 1.0)["out"], img)
