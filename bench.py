@@ -334,6 +334,32 @@ def form_volume(dev):
             "bytes_per_pass_algorithmic_min": 8 * FD * FH * FW, "bytes_per_pass_two_kernels": 28 * FD * FH * FW}
 
 
+def form_gauss(dev, x):
+    """The one-sided Gaussian filter (Algorithm 1 with the one-sided Gaussian kernels of Sec.
+    "Separable Kernels") on the 4096 x 4096 x 3 input: r = 8, sigma = 3 (the paper's sigma
+    for its Gaussian comparisons), 10 passes.  Bound by FP32 arithmetic, not HBM: per frame
+    pixel and pass the separable sums take 8 (r+1) FMAs (2 (r+1) for Up and Dn, 6 (r+1) for
+    the left / right sums of Up, Dn and Fy)."""
+    import torch
+
+    from paper_2108_05021_gb300 import osbf
+
+    r, sigma, it = 8, 3.0, 10
+    out = torch.empty_like(x)
+    t_full = _time(lambda: osbf.filter_gauss(x, r, sigma, it, out=out), 10)
+    t_two = _time(lambda: osbf.filter_gauss(x, r, sigma, 2, out=out), 10)
+    pass_s = (t_full - t_two) / (it - 2)
+    N, C, H, W = x.shape
+    frame_px = N * C * (H + 2 * r) * (W + 2 * r)
+    flops = 16 * (r + 1) * frame_px
+    peak = 152 * 128 * 2 * 2.07e9  # FP32 lanes x 2 flops x maximum SM clock
+    return {"workload": f"{N}x{C}x{H}x{W} float32, r={r}, sigma={sigma}, {it} passes",
+            "gpix_iter_s": x.numel() * it / t_full / 1e9, "ms_per_call": t_full * 1e3,
+            "pass_us": pass_s * 1e6, "pass_flops_algorithmic": flops,
+            "achieved_tflops": flops / pass_s / 1e12, "fp32_peak_tflops_max_clock": peak / 1e12,
+            "frac_of_fp32_peak": flops / pass_s / peak}
+
+
 def form_sweep(dev, x):
     import torch
 
@@ -463,6 +489,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_forms:
         forms = {"fwd_bwd": form_fwd_bwd(dev), "batched": form_batched(dev), "precision": form_precision(dev),
                  "fast_approximation": form_fast(dev, x), "volume_3d": form_volume(dev),
+                 "one_sided_gaussian": form_gauss(dev, x),
                  "sweep_4096x3_30_passes": form_sweep(dev, x),
                  "plain_mpix_iter_s": value}
 

@@ -153,6 +153,29 @@ osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, 
 osbf_status osbf_filter_3d(osbf_ctx *ctx, const float *in, float *out, int N, int C, int D, int H, int W, int r,
                            int iters, uint8_t *maps, void *stream);
 
+/* Largest radius of the one-sided Gaussian filter. */
+#define OSBF_MAX_RADIUS_GAUSS 16
+
+/*
+ * The one-sided Gaussian filter: Algorithm 1 with Phi = a weighted mean whose kernels are
+ * built as in Sec. "Separable Kernels" from the Gaussian k(u) = exp(-u^2 / (2 sigma^2)),
+ * u = -r..r.  Per axis a one-sided kernel k^-/k^+ (distances 0..r from the centre, centre
+ * included on both sides, normalised to sum 1) and the full kernel k (normalised over
+ * -r..r); window N_i's kernel (windows of Eq. (6)-(13)) is the product of the one-sided
+ * kernel on each axis N_i halves and the full kernel on each axis it spans.  First argmin
+ * |mean - U| in the order N1..N8, U <- that mean (Algorithm 2's selection), `iters` passes;
+ * the appendix's boundary (replicate pad by r once, zeros outside the padded frame with
+ * the weights not renormalised there, crop at the end).  sigma = +inf gives flat weights:
+ * the one-sided box filter (up to rounding).  Float32.
+ *   in, out   N x C x H x W (device).
+ *   maps      optional, as for osbf_filter_ex() (same layout and alignment).
+ * Returns OSBF_EINVAL for null pointers, N, C, H or W <= 0, r or iters < 0, sigma not > 0,
+ * in and out overlapping, unaligned or overlapping maps; OSBF_EUNSUPPORTED for
+ * r > OSBF_MAX_RADIUS_GAUSS or N*C > 65535.
+ */
+osbf_status osbf_filter_gauss(osbf_ctx *ctx, const float *in, float *out, int N, int C, int H, int W, int r,
+                              double sigma, int iters, uint8_t *maps, void *stream);
+
 /*
  * Backward (vector-Jacobian product) of the float32 forward, with each pixel's
  * selection frozen to the map stored by the forward (the selection is piecewise

@@ -69,6 +69,8 @@ def _load():
         lib.oracle_filter3d_f64.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp, d, vp]
         lib.oracle_gauss_filter_f64.restype = i
         lib.oracle_gauss_filter_f64.argtypes = [vp, vp, i, i, i, i, i, i, d, vp, vp, d, vp]
+        lib.oracle_gauss_iterate_frame_f64.restype = i
+        lib.oracle_gauss_iterate_frame_f64.argtypes = [vp, i, i, i, i, i, i, d, vp, vp, d, vp]
         lib.oracle_filter_region_f64.restype = i
         lib.oracle_filter_region_f64.argtypes = [vp, i, i, i, i, i, i, i, i, i, vp, vp, i, d, vp]
         lib.oracle_u8_first_pass.restype = i
@@ -232,6 +234,20 @@ def gauss_filter(x: np.ndarray, r: int, iters: int, sigma: float, tie: str = "pa
     _check(_load().oracle_gauss_filter_f64(_ptr(x3), _ptr(out), P, H, W, r, iters, TIE[tie], float(sigma), _ptr(maps),
                                            _ptr(h), float(hint_thresh), ctypes.addressof(nh)))
     return {"out": out.reshape(shape), "maps": maps, "n_hinted": int(nh.value)}
+
+
+def gauss_iterate_frame(frame: np.ndarray, r: int, iters: int, sigma: float, tie: str = "paper",
+                        hint: Optional[np.ndarray] = None, hint_thresh: float = 1e-6) -> np.ndarray:
+    """`iters` one-sided Gaussian passes on already padded frames (P x FH x FW), zeros
+    outside them; no padding or crop.  A (2r+1)^2 patch of a frame, zero where it leaves
+    the frame, gives one pass's value at its centre pixel.  hint: iters x P x FH x FW
+    window indices adopted at near ties (0 = none), as in filter()."""
+    f = np.ascontiguousarray(_planes(frame), dtype=np.float64).copy()
+    P, FH, FW = f.shape
+    h = None if hint is None else np.ascontiguousarray(hint, dtype=np.uint8).reshape(iters, P, FH, FW)
+    _check(_load().oracle_gauss_iterate_frame_f64(_ptr(f), P, FH, FW, r, iters, TIE[tie], float(sigma), None, _ptr(h),
+                                                  float(hint_thresh), None))
+    return f.reshape(np.asarray(frame).shape)
 
 
 def filter_region(plane: np.ndarray, r: int, iters: int, y0: int, y1: int, x0: int, x1: int,

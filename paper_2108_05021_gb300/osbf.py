@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
         L.osbf_filter_fast.restype = st
         L.osbf_filter_3d.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, vp, vp]
         L.osbf_filter_3d.restype = st
+        L.osbf_filter_gauss.argtypes = [vp, vp, vp, i, i, i, i, i, ctypes.c_double, i, vp, vp]
+        L.osbf_filter_gauss.restype = st
         L.osbf_filter_host.argtypes = [vp, vp, vp, i, i, i, i, i, i, i, vp]
         L.osbf_filter_host.restype = st
         L.osbf_filter_backward.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
@@ -225,6 +227,32 @@ def filter_fast(x: torch.Tensor, r: int, iters: int, *, maps: Optional[torch.Ten
     dev = x.device.index
     ctx = context(dev)
     _check(lib().osbf_filter_fast(ctx, x.data_ptr(), out.data_ptr(), N, C, H, W, r, iters, mp, _stream(dev)), ctx)
+    return out
+
+
+def filter_gauss(x: torch.Tensor, r: int, sigma: float, iters: int, *, maps: Optional[torch.Tensor] = None,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """The one-sided Gaussian filter (osbf_filter_gauss; Algorithm 1 with the one-sided
+    Gaussian kernels of Sec. "Separable Kernels") on float32 NCHW input."""
+    _require_cuda(x)
+    N, C, H, W = _nchw(x)
+    if x.dtype != torch.float32:
+        raise TypeError("filter_gauss takes float32")
+    if out is None:
+        out = torch.empty_like(x)
+    _require_cuda(out)
+    if out.dtype != torch.float32 or out.shape != x.shape:
+        raise ValueError("out has the wrong dtype or shape")
+    mp = None
+    if maps is not None:
+        _require_cuda(maps)
+        if maps.dtype != torch.uint8 or tuple(maps.shape) != maps_shape(x, r, iters):
+            raise ValueError(f"maps must be uint8 of shape {maps_shape(x, r, iters)}")
+        mp = maps.data_ptr()
+    dev = x.device.index
+    ctx = context(dev)
+    _check(lib().osbf_filter_gauss(ctx, x.data_ptr(), out.data_ptr(), N, C, H, W, r, float(sigma), iters, mp,
+                                   _stream(dev)), ctx)
     return out
 
 
