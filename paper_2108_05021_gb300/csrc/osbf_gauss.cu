@@ -9,13 +9,13 @@
 // order N1..N8); the appendix's boundary (replicate pad by r once, zeros outside the
 // frame, not renormalised there, crop at the end).
 //
-// Separable sums, one CTA per TH x TW tile of a frame, its region (TH + 2r) x 128 by one
+// Separable sums, one CTA per TH x TW tile of a frame, its region (TH + 2r) x 120 by one
 // TMA box:
 //   pass V (thread = column pair x 8 output rows, packed f32x2 over the pair):
 //     Up(y) = sum_k wh[k] V(y-k),  Dn(y) = sum_k wh[k] V(y+k),
 //     Fy(y) = c (Up + Dn) - wf0 V(y)           (c = wf[k] / wh[k]: the full column mean is
 //                                               the two halves with the centre taken once);
-//   pass H (thread = 8 consecutive outputs of one row): left / right sums
+//   pass H (lane = row, thread = 8 consecutive outputs of its row): left / right sums
 //     L(X)(x) = sum_k wh[k] X(x-k), Rt(X)(x) = sum_k wh[k] X(x+k) of the pair {Up, Dn}
 //     (packed) and of Fy, then
 //       N1 = L(Dn), N2 = Rt(Dn), N3 = Rt(Up), N4 = L(Up), N5 = L(Fy), N6 = Rt(Fy),
@@ -37,97 +37,93 @@ unsigned int *osbf_ctx_err_word(osbf_ctx *ctx);
 namespace osbf {
 namespace vg {
 
-// NT threads; TH output rows per tile (4 pass-V segments of SEG rows); every tile region
-// is RW = 128 columns wide, its TW = RW - 2 RP output columns centred (RP = r rounded up to
-// a multiple of 4, so region and output columns both start on 16 bytes); G outputs per
-// pass-H thread.
-constexpr int NT = 256, TH = 32, SEG = 8, RW = 128, G = 8;
-static_assert(TH == SEG * (NT / (RW / 2)), "pass V: one thread per column pair and segment");
+// NT threads; TH output rows per tile (4 pass-V segments of SEG rows; in pass H lane = row);
+// every tile region is RW = 120 columns wide, its TW = RW - 2 RP output columns centred (RP
+// = r rounded up to a multiple of 4, so region and output columns both start on 16 bytes);
+// G outputs per pass-H thread.
+constexpr int NT = 256, TH = 32, SEG = 8, RW = 120, G = 8;
+static_assert(TH == 32 && TH == SEG * (NT / 64), "pass V: column pair x segment; pass H: lane = row");
+// Row pitches (floats) of the shared fields, odd numbers of 16-byte chunks: the lane = row
+// 16-byte loads of pass H fall on distinct banks in every 8-lane phase.  VP is also the
+// TMA box width (4 columns past the region, unused).
+constexpr int VP = RW + 4, UDP = 2 * RW + 4, FP = RW + 4;
+static_assert((VP / 4) % 2 == 1 && (UDP / 4) % 2 == 1 && (FP / 4) % 2 == 1, "odd chunk pitches");
 
 __host__ __device__ constexpr int rp(int R) { return (R + 3) / 4 * 4; }
 __host__ __device__ constexpr int r2(int R) { return (R + 1) / 2 * 2; }
 __host__ __device__ constexpr int tw(int R) { return RW - 2 * rp(R); }
 __host__ __device__ constexpr int rh(int R) { return TH + 2 * R; }
-// shared layout (bytes): the region V (RH x RW floats, as the TMA box lands), the {Up, Dn}
-// pairs (TH x RW float2, 16-byte chunks swizzled), Fy (TH x RW floats, chunks swizzled), the
-// mbarrier
-__host__ __device__ constexpr int off_ud(int R) { return rh(R) * RW * 4; }
-__host__ __device__ constexpr int off_f(int R) { return off_ud(R) + TH * RW * 8; }
-__host__ __device__ constexpr int smem_bytes(int R) { return off_f(R) + TH * RW * 4 + 16; }
-
-// The chunk swizzles keep pass H's strided 16-byte loads (lane stride G/2 chunks of
-// {Up, Dn}, G/4 chunks of Fy) on distinct banks within each 8-lane phase.
-__device__ __forceinline__ int ud_chunk(int q) { return q ^ ((q >> 3) & 3); }
-__device__ __forceinline__ int f_chunk(int q) { return q ^ ((q >> 3) & 1); }
+// shared layout (bytes): the region V (RH rows of VP floats, as the TMA box lands), the
+// {Up, Dn} pairs (TH rows of UDP floats), Fy (TH rows of FP floats), the mbarrier
+__host__ __device__ constexpr int off_ud(int R) { return rh(R) * VP * 4; }
+__host__ __device__ constexpr int off_f(int R) { return off_ud(R) + TH * UDP * 4; }
+__host__ __device__ constexpr int smem_bytes(int R) { return off_f(R) + TH * FP * 4 + 16; }
 
 struct GaussParams {
-    float wh[OSBF_MAX_RADIUS_GAUSS + 1];  // one-sided weights, distance 0..r
-    float c, wf0;                         // wf[k] / wh[k] and wf[0]
-    float *dst;                           // next frame: P x FH x FWp
-    uint8_t *maps;                        // this pass's maps (P x FH x map_pitch) or null
+    float2 wh2[OSBF_MAX_RADIUS_GAUSS + 1];  // {wh[k], wh[k]}: one-sided weights, distance 0..r
+    float wh[OSBF_MAX_RADIUS_GAUSS + 1];
+    float2 c2, m2;                          // {wf[k] / wh[k]} and {-wf[0]}, pairs
+    float *dst;                             // next frame: P x FH x FWp
+    uint8_t *maps;                          // this pass's maps (P x FH x map_pitch) or null
     long long dst_plane, map_plane;
     int map_pitch, FH, FW, FWp, tiles_x;
-    unsigned int *err;                    // bit 0: a tile load did not land in time
+    unsigned int *err;                      // bit 0: a tile load did not land in time
 };
 
-__device__ __forceinline__ float2 bc(float w) { return make_float2(w, w); }
-
-// pass V: thread = column pair cp and a segment of SEG output rows; region rows
+// pass V: thread = column pair cp (< RW/2) and a segment of SEG output rows; region rows
 // seg*SEG + j, j = 0..SEG+2R-1, enter one at a time; output row i of the segment is region
 // row i + R.
 template <int R>
-__device__ __forceinline__ void pass_v(const float *bV, float4 *ud, float4 *fy, const GaussParams &q) {
-    const int cp = threadIdx.x & (RW / 2 - 1), seg = threadIdx.x / (RW / 2);
-    const float2 *src = reinterpret_cast<const float2 *>(bV) + seg * SEG * (RW / 2) + cp;
-    const float2 c2 = bc(q.c), m2 = bc(-q.wf0);
+__device__ __forceinline__ void pass_v(const float *bV, float *ud, float *fy, const GaussParams &q) {
+    const int cp = threadIdx.x & 63, seg = threadIdx.x >> 6;
+    if (cp >= RW / 2) return;
+    const float *src = bV + seg * SEG * VP + 2 * cp;
+    const float2 c2 = q.c2, m2 = q.m2;
     float2 up[SEG], dn[SEG], fc[SEG];
 #pragma unroll
     for (int j = 0; j < SEG + 2 * R; ++j) {
-        const float2 v = src[j * (RW / 2)];
+        const float2 v = *reinterpret_cast<const float2 *>(src + j * VP);
 #pragma unroll
         for (int i = 0; i < SEG; ++i) {
             const int kl = i + R - j, kr = j - i - R;  // tap distance for Up(i) / Dn(i)
-            if (kl >= 0 && kl <= R) up[i] = kl == R ? v2::mul2(bc(q.wh[kl]), v) : v2::fma2(bc(q.wh[kl]), v, up[i]);
-            if (kr >= 0 && kr <= R) dn[i] = kr == 0 ? v2::mul2(bc(q.wh[kr]), v) : v2::fma2(bc(q.wh[kr]), v, dn[i]);
+            if (kl >= 0 && kl <= R) up[i] = kl == R ? v2::mul2(q.wh2[kl], v) : v2::fma2(q.wh2[kl], v, up[i]);
+            if (kr >= 0 && kr <= R) dn[i] = kr == 0 ? v2::mul2(q.wh2[kr], v) : v2::fma2(q.wh2[kr], v, dn[i]);
             if (kr == 0) fc[i] = v2::mul2(m2, v);
             if (kr == R) {  // row i complete
                 const float2 f = v2::fma2(c2, v2::add2(up[i], dn[i]), fc[i]);
                 const int o = seg * SEG + i;
-                ud[o * (RW / 2) + ud_chunk(cp)] = make_float4(up[i].x, dn[i].x, up[i].y, dn[i].y);
-                reinterpret_cast<float2 *>(fy + o * (RW / 4) + f_chunk(cp >> 1))[cp & 1] = f;
+                *reinterpret_cast<float4 *>(ud + o * UDP + 4 * cp) = make_float4(up[i].x, dn[i].x, up[i].y, dn[i].y);
+                *reinterpret_cast<float2 *>(fy + o * FP + 2 * cp) = f;
             }
         }
     }
 }
 
-// pass H: thread = G consecutive outputs (region columns c0..c0+G-1) of one output row.
+// pass H: lane = output row, warp = a group of G consecutive output columns (region columns
+// c0..c0+G-1).  Selection by signed differences d_i = mean_i - U, first argmin |d_i| in
+// the order N1..N8, U <- U + d (Algorithm 2).  Evaluated as the best of N1..N4 merged with
+// the best of N7, N8 (once both sums of an output are complete), then N5, N6: a later
+// window replaces the best only when strictly closer, N5 / N6 also on an equal |d| held by
+// N7 / N8 (they come first in the order).
 template <int R>
-__device__ __forceinline__ void pass_h(const float *bV, const float4 *ud, const float4 *fy, const GaussParams &q,
+__device__ __forceinline__ void pass_h(const float *bV, const float *ud, const float *fy, const GaussParams &q,
                                        int plane, int ty0, int tx0) {
     constexpr int RP = rp(R), R2 = r2(R), TW = tw(R), NG = TW / G;
-    constexpr int NUD = (G + 2 * R2) / 2;  // chunks of {Up, Dn} pairs, from column c0 - R2
-    constexpr int NF = (G + 2 * RP) / 4;   // chunks of Fy, from column c0 - RP
+    constexpr int NUD = (G + 2 * R2) / 2;  // 16-byte chunks of {Up, Dn} pairs, from column c0 - R2
+    constexpr int NF = (G + 2 * RP) / 4;   // 16-byte chunks of Fy, from column c0 - RP
     static_assert(TW % G == 0 && G % 4 == 0, "output groups of whole 16-byte chunks");
-    const float2 c2 = bc(q.c), m2 = bc(-q.wf0);
-    for (int it = threadIdx.x; it < TH * NG; it += NT) {
-        const int row = it / NG, g = it - row * NG;
+    const int row = threadIdx.x & 31;
+    const float2 c2 = q.c2, m2 = q.m2;
+    for (int g = threadIdx.x >> 5; g < NG; g += NT / 32) {
         const int c0 = RP + G * g;
-        float u[G];
-#pragma unroll
-        for (int h = 0; h < G / 4; ++h) {
-            const float4 t = reinterpret_cast<const float4 *>(bV + (row + R) * RW + c0)[h];
-            u[4 * h] = t.x;
-            u[4 * h + 1] = t.y;
-            u[4 * h + 2] = t.z;
-            u[4 * h + 3] = t.w;
-        }
-        // {Up, Dn}: left and right sums, the centre pair for the full-row means
+        const float *urow = bV + (row + R) * VP + c0;  // the outputs' own values U, read where used
+        float bd[G];          // best signed difference so far
+        int bi[G];            // its window (tracked also without maps: the register schedule spills less)
         float2 lt[G], rt[G], xc[G];
-        const float4 *udr = ud + row * (RW / 2);
-        const int q0 = (c0 - R2) >> 1;
+        const float4 *udr = reinterpret_cast<const float4 *>(ud + row * UDP + 2 * (c0 - R2));
 #pragma unroll
         for (int m = 0; m < NUD; ++m) {
-            const float4 t = udr[ud_chunk(q0 + m)];
+            const float4 t = udr[m];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const float2 v = h ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
@@ -135,45 +131,37 @@ __device__ __forceinline__ void pass_h(const float *bV, const float4 *ud, const 
 #pragma unroll
                 for (int o = 0; o < G; ++o) {
                     const int kl = o + R2 - p, kr = p - R2 - o;
-                    if (kl >= 0 && kl <= R)
-                        lt[o] = kl == R ? v2::mul2(bc(q.wh[kl]), v) : v2::fma2(bc(q.wh[kl]), v, lt[o]);
-                    if (kr >= 0 && kr <= R)
-                        rt[o] = kr == 0 ? v2::mul2(bc(q.wh[kr]), v) : v2::fma2(bc(q.wh[kr]), v, rt[o]);
+                    if (kl >= 0 && kl <= R) lt[o] = kl == R ? v2::mul2(q.wh2[kl], v) : v2::fma2(q.wh2[kl], v, lt[o]);
+                    if (kr >= 0 && kr <= R) rt[o] = kr == 0 ? v2::mul2(q.wh2[kr], v) : v2::fma2(q.wh2[kr], v, rt[o]);
                     if (kr == 0) xc[o] = v2::mul2(m2, v);
+                    if (kr == R) {  // both sums of output o complete: N1..N4, N7, N8
+                        const float2 f = v2::fma2(c2, v2::add2(lt[o], rt[o]), xc[o]);  // {N8, N7}
+                        const float uo = urow[o];
+                        float d = lt[o].y - uo;
+                        int i = 1;
+                        float t2 = rt[o].y - uo;
+                        if (fabsf(t2) < fabsf(d)) { d = t2; i = 2; }
+                        t2 = rt[o].x - uo;
+                        if (fabsf(t2) < fabsf(d)) { d = t2; i = 3; }
+                        t2 = lt[o].x - uo;
+                        if (fabsf(t2) < fabsf(d)) { d = t2; i = 4; }
+                        float db = f.y - uo;
+                        int ib = 7;
+                        t2 = f.x - uo;
+                        if (fabsf(t2) < fabsf(db)) { db = t2; ib = 8; }
+                        if (fabsf(db) < fabsf(d)) { d = db; i = ib; }
+                        bd[o] = d;
+                        bi[o] = i;
+                    }
                 }
             }
         }
-        // candidates N1..N4 (best A) and N7, N8 (best B), first argmin within each group
-        float bA[G], aA[G], bB[G], aB[G];
-        int iA[G], iB[G];
-#pragma unroll
-        for (int o = 0; o < G; ++o) {
-            const float2 f = v2::fma2(c2, v2::add2(lt[o], rt[o]), xc[o]);  // {N8, N7}
-            const float m1 = lt[o].y, mm2 = rt[o].y, m3 = rt[o].x, m4 = lt[o].x;
-            float b = m1, a = fabsf(m1 - u[o]);
-            int i = 1;
-            float t = fabsf(mm2 - u[o]);
-            if (t < a) { b = mm2; a = t; i = 2; }
-            t = fabsf(m3 - u[o]);
-            if (t < a) { b = m3; a = t; i = 3; }
-            t = fabsf(m4 - u[o]);
-            if (t < a) { b = m4; a = t; i = 4; }
-            bA[o] = b;
-            aA[o] = a;
-            iA[o] = i;
-            const float a7 = fabsf(f.y - u[o]), a8 = fabsf(f.x - u[o]);
-            const bool p8 = a8 < a7;
-            bB[o] = p8 ? f.x : f.y;
-            aB[o] = p8 ? a8 : a7;
-            iB[o] = p8 ? 8 : 7;
-        }
         // Fy: left and right sums (N5, N6)
         float lf[G], rf[G];
-        const float4 *fr = fy + row * (RW / 4);
-        const int f0 = (c0 - RP) >> 2;
+        const float4 *fr = reinterpret_cast<const float4 *>(fy + row * FP + (c0 - RP));
 #pragma unroll
         for (int m = 0; m < NF; ++m) {
-            const float4 t = fr[f_chunk(f0 + m)];
+            const float4 t = fr[m];
             const float tv[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -183,50 +171,48 @@ __device__ __forceinline__ void pass_h(const float *bV, const float4 *ud, const 
                     const int kl = o + RP - p, kr = p - RP - o;
                     if (kl >= 0 && kl <= R) lf[o] = kl == R ? q.wh[kl] * tv[h] : fmaf(q.wh[kl], tv[h], lf[o]);
                     if (kr >= 0 && kr <= R) rf[o] = kr == 0 ? q.wh[kr] * tv[h] : fmaf(q.wh[kr], tv[h], rf[o]);
+                    if (kr == R) {
+                        float d = bd[o];
+                        int i = bi[o];
+                        const float uo = urow[o];
+                        const float d5 = lf[o] - uo, d6 = rf[o] - uo;
+                        if (fabsf(d5) < fabsf(d) || (i >= 7 && fabsf(d5) == fabsf(d))) { d = d5; i = 5; }
+                        if (fabsf(d6) < fabsf(d) || (i >= 7 && fabsf(d6) == fabsf(d))) { d = d6; i = 6; }
+                        bd[o] = uo + d;  // the updated value
+                        bi[o] = i;
+                    }
                 }
             }
         }
-        float res[G];
-        uint8_t sel[G];
-#pragma unroll
-        for (int o = 0; o < G; ++o) {  // order: N1..N4, N5, N6, N7..N8
-            float b = bA[o], a = aA[o];
-            int i = iA[o];
-            float t = fabsf(lf[o] - u[o]);
-            if (t < a) { b = lf[o]; a = t; i = 5; }
-            t = fabsf(rf[o] - u[o]);
-            if (t < a) { b = rf[o]; a = t; i = 6; }
-            if (aB[o] < a) { b = bB[o]; i = iB[o]; }
-            res[o] = b;
-            sel[o] = (uint8_t)i;
-        }
         const int y = ty0 + row, x = tx0 + G * g;
         if (y < q.FH && x < q.FW) {
-            float *d = q.dst + (long long)plane * q.dst_plane + (long long)y * q.FWp + x;
+            float *dp = q.dst + (long long)plane * q.dst_plane + (long long)y * q.FWp + x;
 #pragma unroll
             for (int h = 0; h < G / 4; ++h)  // rows are padded to 4 floats: a started 4-vector fits
                 if (x + 4 * h < q.FW)
-                    reinterpret_cast<float4 *>(d)[h] = make_float4(res[4 * h], res[4 * h + 1], res[4 * h + 2], res[4 * h + 3]);
+                    reinterpret_cast<float4 *>(dp)[h] = make_float4(bd[4 * h], bd[4 * h + 1], bd[4 * h + 2], bd[4 * h + 3]);
             if (q.maps) {
                 uint8_t *mp = q.maps + (long long)plane * q.map_plane + (long long)y * q.map_pitch + x;
-                uint32_t w[G / 4];
-#pragma unroll
-                for (int h = 0; h < G / 4; ++h)
-                    w[h] = sel[4 * h] | (sel[4 * h + 1] << 8) | (sel[4 * h + 2] << 16) | ((uint32_t)sel[4 * h + 3] << 24);
 #pragma unroll
                 for (int h = 0; h < G / 4; ++h)  // map rows are padded to 16 bytes
-                    if (x + 4 * h < q.FW) reinterpret_cast<uint32_t *>(mp)[h] = w[h];
+                    if (x + 4 * h < q.FW)
+                        reinterpret_cast<uint32_t *>(mp)[h] = (uint32_t)bi[4 * h] | ((uint32_t)bi[4 * h + 1] << 8) |
+                                                              ((uint32_t)bi[4 * h + 2] << 16) |
+                                                              ((uint32_t)bi[4 * h + 3] << 24);
             }
         }
     }
 }
 
+// CTAs per SM the shared layout allows (228 KB per SM, 1 KB reserved per CTA)
+__host__ __device__ constexpr int ctas_per_sm(int R) { return 228 * 1024 / (smem_bytes(R) + 1024); }
+
 template <int R>
-__global__ void __launch_bounds__(NT, 3) gauss_kernel(const __grid_constant__ CUtensorMap src, const GaussParams q) {
+__global__ void __launch_bounds__(NT, ctas_per_sm(R) >= 3 ? 3 : 2) gauss_kernel(const __grid_constant__ CUtensorMap src, const GaussParams q) {
     extern __shared__ __align__(128) unsigned char smg[];
     float *bV = reinterpret_cast<float *>(smg);
-    float4 *ud = reinterpret_cast<float4 *>(smg + off_ud(R));
-    float4 *fy = reinterpret_cast<float4 *>(smg + off_f(R));
+    float *ud = reinterpret_cast<float *>(smg + off_ud(R));
+    float *fy = reinterpret_cast<float *>(smg + off_f(R));
     const uint32_t bar = v2::smem_u32(smg + smem_bytes(R) - 16);
     const int tile = blockIdx.x, plane = blockIdx.y;
     const int ty0 = (tile / q.tiles_x) * TH, tx0 = (tile % q.tiles_x) * tw(R);
@@ -234,7 +220,7 @@ __global__ void __launch_bounds__(NT, 3) gauss_kernel(const __grid_constant__ CU
         v2::mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         v2::fence_proxy_async();
-        v2::tma_load_3d(v2::smem_u32(bV), &src, tx0 - rp(R), ty0 - R, plane, bar, (uint32_t)(rh(R) * RW * 4));
+        v2::tma_load_3d(v2::smem_u32(bV), &src, tx0 - rp(R), ty0 - R, plane, bar, (uint32_t)(rh(R) * VP * 4));
     }
     __syncthreads();
     const bool timed_out = !v2::mbar_wait_bounded(bar, 0);
@@ -327,9 +313,12 @@ extern "C" osbf_status osbf_filter_gauss(osbf_ctx *ctx, const float *in, float *
             sh += g[k];
             sf += k == 0 ? g[k] : 2.0 * g[k];
         }
-        for (int k = 0; k <= r; ++k) q.wh[k] = (float)(g[k] / sh);
-        q.c = (float)(sh / sf);
-        q.wf0 = (float)(g[0] / sf);
+        for (int k = 0; k <= r; ++k) {
+            q.wh[k] = (float)(g[k] / sh);
+            q.wh2[k] = make_float2(q.wh[k], q.wh[k]);
+        }
+        q.c2 = make_float2((float)(sh / sf), (float)(sh / sf));
+        q.m2 = make_float2((float)(-g[0] / sf), (float)(-g[0] / sf));
     }
     const size_t fbytes = sizeof(float) * (size_t)P * FH * FWp;
     osbf_status st;
@@ -353,7 +342,7 @@ extern "C" osbf_status osbf_filter_gauss(osbf_ctx *ctx, const float *in, float *
     int cur = 0;
     for (int pass = 0; pass < iters; ++pass) {
         CUtensorMap m;
-        if (!encode_frame_map(&m, Storage::F32, fr[cur], FW, FH, (int)P, FWp, vg::RW, vg::region_rows(r)))
+        if (!encode_frame_map(&m, Storage::F32, fr[cur], FW, FH, (int)P, FWp, vg::VP, vg::region_rows(r)))
             return osbf_ctx_fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (Gaussian frame)");
         q.dst = fr[1 - cur];
         q.maps = maps ? maps + (long long)pass * mstride : nullptr;
