@@ -388,6 +388,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other forms (for profiling runs)")
+    ap.add_argument("--form", default=None,
+                    choices=["fwd_bwd", "batched", "precision", "fast_approximation", "volume_3d", "one_sided_gaussian"],
+                    help="run only this form on one GPU and print its JSON (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -411,6 +414,12 @@ def main():
 
     x_np = synth.piecewise_stack(N_, C_, H_, W_, seed=rank, sigma=0.05)
     x = torch.from_numpy(x_np).to(dev)
+    if args.form is not None:
+        one = {"fwd_bwd": lambda: form_fwd_bwd(dev), "batched": lambda: form_batched(dev),
+               "precision": lambda: form_precision(dev), "fast_approximation": lambda: form_fast(dev, x),
+               "volume_3d": lambda: form_volume(dev), "one_sided_gaussian": lambda: form_gauss(dev, x)}[args.form]
+        print(json.dumps({"form": args.form, "result": one()}))
+        return
     out = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
 
