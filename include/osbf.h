@@ -108,8 +108,10 @@ osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int 
 
 /*
  * osbf_filter() on HOST buffers: copies `in` to the device, filters, copies the
- * result into `out`, and returns when `out` is filled (synchronous).  Pinned host
- * memory gives the fastest copies.  The device buffers are owned by the context.
+ * result into `out`, and returns when `out` is filled (synchronous).  The N*C planes
+ * go in up to four chunks: a chunk's copies (on two streams owned by the context) overlap
+ * the filtering of its neighbours on `stream`.  Pinned host memory gives the fastest
+ * copies and the overlap.  The device buffers are owned by the context.
  */
 osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,
                              osbf_dtype dtype, void *stream);

@@ -1,5 +1,6 @@
 // osbf_api.cu -- the C ABI of libosbf.so (see include/osbf.h): argument checks,
 // workspace, the sequence of fused-group launches, host-buffer calls, tuning.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +23,8 @@ struct osbf_ctx {
     size_t frame_bytes[2] = {0, 0};
     void *dev_in = nullptr, *dev_out = nullptr;  // osbf_filter_host staging
     size_t dev_in_bytes = 0, dev_out_bytes = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;  // osbf_filter_host copy streams
+    cudaEvent_t ev_start = nullptr, ev_in[4] = {}, ev_done[4] = {};
     void *ws[4] = {nullptr, nullptr, nullptr, nullptr};  // backward / checkpoint workspaces
     size_t ws_bytes[4] = {0, 0, 0, 0};
     int last_launches = 0;
@@ -411,6 +414,13 @@ void osbf_destroy(osbf_ctx *ctx) {
         if (p) cudaFree(p);
     if (ctx->dev_in) cudaFree(ctx->dev_in);
     if (ctx->dev_out) cudaFree(ctx->dev_out);
+    if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    for (int k = 0; k < 4; ++k) {
+        if (ctx->ev_in[k]) cudaEventDestroy(ctx->ev_in[k]);
+        if (ctx->ev_done[k]) cudaEventDestroy(ctx->ev_done[k]);
+    }
     if (ctx->err_word) cudaFree(ctx->err_word);
     osbf_batched_free(ctx);
     delete ctx;
@@ -513,10 +523,49 @@ osbf_status osbf_filter_host(osbf_ctx *ctx, const void *in, void *out, int N, in
     e = ensure(ctx, &ctx->dev_out, &ctx->dev_out_bytes, out_bytes);
     if (e) return e;
     cudaStream_t s = (cudaStream_t)stream;
-    OSBF_CK(cudaMemcpyAsync(ctx->dev_in, in, in_bytes, cudaMemcpyHostToDevice, s));
-    e = osbf_filter_ex(ctx, ctx->dev_in, ctx->dev_out, N, C, H, W, r, iters, dtype, nullptr, stream);
-    if (e) return e;
-    OSBF_CK(cudaMemcpyAsync(out, ctx->dev_out, out_bytes, cudaMemcpyDeviceToHost, s));
+    // Planes are independent: up to four plane chunks, each copied in on one stream,
+    // filtered on the caller's stream once its copy has landed, and copied out on a third
+    // stream once filtered -- the copies of one chunk overlap the filtering of another.
+    if (!ctx->copy_in) {
+        OSBF_CK(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
+        OSBF_CK(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+        OSBF_CK(cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+        for (int k = 0; k < 4; ++k) {
+            OSBF_CK(cudaEventCreateWithFlags(&ctx->ev_in[k], cudaEventDisableTiming));
+            OSBF_CK(cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming));
+        }
+    }
+    const int K = (int)std::min<long long>(P, 4);
+    const size_t pin = in_bytes / (size_t)P, pout = out_bytes / (size_t)P;  // bytes per plane
+    // the staging buffers are free once the caller's stream has finished earlier work
+    OSBF_CK(cudaEventRecord(ctx->ev_start, s));
+    OSBF_CK(cudaStreamWaitEvent(ctx->copy_in, ctx->ev_start, 0));
+    OSBF_CK(cudaStreamWaitEvent(ctx->copy_out, ctx->ev_start, 0));
+    long long p0[5];
+    for (int c = 0; c <= K; ++c) p0[c] = P * c / K;
+    for (int c = 0; c < K; ++c) {
+        OSBF_CK(cudaMemcpyAsync((char *)ctx->dev_in + p0[c] * pin, (const char *)in + p0[c] * pin,
+                                (size_t)(p0[c + 1] - p0[c]) * pin, cudaMemcpyHostToDevice, ctx->copy_in));
+        OSBF_CK(cudaEventRecord(ctx->ev_in[c], ctx->copy_in));
+    }
+    int launches = 0;
+    for (int c = 0; c < K; ++c) {
+        OSBF_CK(cudaStreamWaitEvent(s, ctx->ev_in[c], 0));
+        e = osbf_filter_ex(ctx, (const char *)ctx->dev_in + p0[c] * pin, (char *)ctx->dev_out + p0[c] * pout,
+                           (int)(p0[c + 1] - p0[c]), 1, H, W, r, iters, dtype, nullptr, stream);
+        if (e) {
+            cudaStreamSynchronize(ctx->copy_in);
+            cudaStreamSynchronize(ctx->copy_out);
+            return e;
+        }
+        launches += ctx->last_launches;
+        OSBF_CK(cudaEventRecord(ctx->ev_done[c], s));
+        OSBF_CK(cudaStreamWaitEvent(ctx->copy_out, ctx->ev_done[c], 0));
+        OSBF_CK(cudaMemcpyAsync((char *)out + p0[c] * pout, (const char *)ctx->dev_out + p0[c] * pout,
+                                (size_t)(p0[c + 1] - p0[c]) * pout, cudaMemcpyDeviceToHost, ctx->copy_out));
+    }
+    ctx->last_launches = launches;
+    OSBF_CK(cudaStreamSynchronize(ctx->copy_out));
     OSBF_CK(cudaStreamSynchronize(s));
     unsigned int w = 0;
     OSBF_CK(cudaMemcpy(&w, ctx->err_word, sizeof w, cudaMemcpyDeviceToHost));
