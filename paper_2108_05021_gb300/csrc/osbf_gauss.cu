@@ -101,11 +101,11 @@ __device__ __forceinline__ void pass_v(const float *bV, float *ud, float *fy, co
 
 // pass H: lane = output row, warp = a group of G consecutive output columns (region columns
 // c0..c0+G-1).  Selection by signed differences d_i = mean_i - U, first argmin |d_i| in
-// the order N1..N8, U <- U + d (Algorithm 2).  Evaluated as the best of N1..N4 merged with
-// the best of N7, N8 (once both sums of an output are complete), then N5, N6: a later
-// window replaces the best only when strictly closer, N5 / N6 also on an equal |d| held by
-// N7 / N8 (they come first in the order).
-template <int R>
+// the order N1..N8, U <- U + d (Algorithm 2).  Evaluated in that order as three groups:
+// once both sums of an output are complete, the best of N1..N4 and, kept apart, the best
+// of N7, N8; after the Fy sums, N5 and N6 against the first, then the N7 / N8 winner -- a
+// later window replaces the best only when strictly closer.
+template <int R, bool MAPS>
 __device__ __forceinline__ void pass_h(const float *bV, const float *ud, const float *fy, const GaussParams &q,
                                        int plane, int ty0, int tx0) {
     constexpr int RP = rp(R), R2 = r2(R), TW = tw(R), NG = TW / G;
@@ -117,8 +117,8 @@ __device__ __forceinline__ void pass_h(const float *bV, const float *ud, const f
     for (int g = threadIdx.x >> 5; g < NG; g += NT / 32) {
         const int c0 = RP + G * g;
         const float *urow = bV + (row + R) * VP + c0;  // the outputs' own values U, read where used
-        float bd[G];          // best signed difference so far
-        int bi[G];            // its window (tracked also without maps: the register schedule spills less)
+        float bd[G], bb[G];   // best signed difference of N1..N4 / of N7, N8
+        int bi[G];            // MAPS: their windows (low / high nibble), then the chosen one
         float2 lt[G], rt[G], xc[G];
         const float4 *udr = reinterpret_cast<const float4 *>(ud + row * UDP + 2 * (c0 - R2));
 #pragma unroll
@@ -149,9 +149,9 @@ __device__ __forceinline__ void pass_h(const float *bV, const float *ud, const f
                         int ib = 7;
                         t2 = f.x - uo;
                         if (fabsf(t2) < fabsf(db)) { db = t2; ib = 8; }
-                        if (fabsf(db) < fabsf(d)) { d = db; i = ib; }
                         bd[o] = d;
-                        bi[o] = i;
+                        bb[o] = db;
+                        if (MAPS) bi[o] = i | (ib << 4);
                     }
                 }
             }
@@ -173,13 +173,14 @@ __device__ __forceinline__ void pass_h(const float *bV, const float *ud, const f
                     if (kr >= 0 && kr <= R) rf[o] = kr == 0 ? q.wh[kr] * tv[h] : fmaf(q.wh[kr], tv[h], rf[o]);
                     if (kr == R) {
                         float d = bd[o];
-                        int i = bi[o];
+                        int i = MAPS ? bi[o] & 15 : 0;
                         const float uo = urow[o];
                         const float d5 = lf[o] - uo, d6 = rf[o] - uo;
-                        if (fabsf(d5) < fabsf(d) || (i >= 7 && fabsf(d5) == fabsf(d))) { d = d5; i = 5; }
-                        if (fabsf(d6) < fabsf(d) || (i >= 7 && fabsf(d6) == fabsf(d))) { d = d6; i = 6; }
+                        if (fabsf(d5) < fabsf(d)) { d = d5; i = 5; }
+                        if (fabsf(d6) < fabsf(d)) { d = d6; i = 6; }
+                        if (fabsf(bb[o]) < fabsf(d)) { d = bb[o]; i = MAPS ? bi[o] >> 4 : 0; }
                         bd[o] = uo + d;  // the updated value
-                        bi[o] = i;
+                        if (MAPS) bi[o] = i;
                     }
                 }
             }
@@ -191,7 +192,7 @@ __device__ __forceinline__ void pass_h(const float *bV, const float *ud, const f
             for (int h = 0; h < G / 4; ++h)  // rows are padded to 4 floats: a started 4-vector fits
                 if (x + 4 * h < q.FW)
                     reinterpret_cast<float4 *>(dp)[h] = make_float4(bd[4 * h], bd[4 * h + 1], bd[4 * h + 2], bd[4 * h + 3]);
-            if (q.maps) {
+            if (MAPS) {
                 uint8_t *mp = q.maps + (long long)plane * q.map_plane + (long long)y * q.map_pitch + x;
 #pragma unroll
                 for (int h = 0; h < G / 4; ++h)  // map rows are padded to 16 bytes
@@ -207,7 +208,7 @@ __device__ __forceinline__ void pass_h(const float *bV, const float *ud, const f
 // CTAs per SM the shared layout allows (228 KB per SM, 1 KB reserved per CTA)
 __host__ __device__ constexpr int ctas_per_sm(int R) { return 228 * 1024 / (smem_bytes(R) + 1024); }
 
-template <int R>
+template <int R, bool MAPS>
 __global__ void __launch_bounds__(NT, ctas_per_sm(R) >= 3 ? 3 : 2) gauss_kernel(const __grid_constant__ CUtensorMap src, const GaussParams q) {
     extern __shared__ __align__(128) unsigned char smg[];
     float *bV = reinterpret_cast<float *>(smg);
@@ -233,19 +234,25 @@ __global__ void __launch_bounds__(NT, ctas_per_sm(R) >= 3 ? 3 : 2) gauss_kernel(
     }
     pass_v<R>(bV, ud, fy, q);
     __syncthreads();
-    pass_h<R>(bV, ud, fy, q, plane, ty0, tx0);
+    pass_h<R, MAPS>(bV, ud, fy, q, plane, ty0, tx0);
+}
+
+template <int R, bool MAPS>
+cudaError_t launch_m(const CUtensorMap &m, const GaussParams &q, int tiles, int P, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(gauss_kernel<R, MAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(R));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gauss_kernel<R, MAPS><<<dim3(tiles, P), NT, smem_bytes(R), s>>>(m, q);
+    return cudaGetLastError();
 }
 
 template <int R>
 cudaError_t launch(const CUtensorMap &m, const GaussParams &q, int tiles, int P, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gauss_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(R));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    gauss_kernel<R><<<dim3(tiles, P), NT, smem_bytes(R), s>>>(m, q);
-    return cudaGetLastError();
+    return q.maps ? launch_m<R, true>(m, q, tiles, P, s) : launch_m<R, false>(m, q, tiles, P, s);
 }
 
 cudaError_t launch_r(int r, const CUtensorMap &m, const GaussParams &q, int tiles, int P, cudaStream_t s) {
