@@ -282,13 +282,13 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         const int Dg = iters - passes < D ? iters - passes : D;
         const bool last = passes + Dg == iters;
         // one pass written straight from registers into the destination: a frame, or the
-        // cropped output when its rows hold 16-byte aligned 4-vectors (W % 4 == 0, r % 4 == 0).
-        // float32 frames: any r (the tile grid shifts so the halo stays exactly r columns);
-        // 16-bit frames: r % 8 == 0 (a 16-byte aligned halo)
+        // cropped output when its rows hold aligned 4-vectors (W % 4 == 0, r % 4 == 0); any r
+        // (the tile grid shifts so the halo stays exactly r columns while the TMA box starts
+        // on 16 bytes)
         const bool last_out = passes + Dg == iters && !out_is_frame;
         const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
                                           ((uintptr_t)out % (st == Storage::F32 ? 16 : 8)) == 0);
-        const bool direct = Dg == 1 && tie == 0 && out_ok && (st == Storage::F32 || r % 8 == 0);
+        const bool direct = Dg == 1 && tie == 0 && out_ok;
         // float32 single passes at r % 4 == 0 (no maps) from frame to frame: results leave
         // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
         // stores (the last pass, into the cropped output, keeps the register stores and
@@ -297,7 +297,7 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
                               : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
                                                    : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
-        const int shift = (direct && st == Storage::F32) ? (4 - r % 4) % 4 : 0;
+        const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
         CUtensorMap map;
         if (!encode_frame_map(&map, st, src, FW, FH, P, src_pitch, L.BX, L.RH0))
             return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame %dx%dx%d, pitch %d)", FW, FH, P,

@@ -51,9 +51,10 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     Layout2 L;
     const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
     L.EY = D * R;
-    // direct float32 kernels keep the halo at exactly R columns; the tile grid is shifted
-    // by (4 - R % 4) % 4 columns instead, so the TMA box still starts on 16 bytes
-    L.EX = (direct && sizeof(T) == 4) ? D * R : round_up(D * R, xa);
+    // direct kernels keep the halo at exactly R columns; the tile grid is shifted instead
+    // (float32: by (4 - R % 4) % 4 columns, 16-bit: by (8 - R % 8) % 8), so the TMA box
+    // still starts on 16 bytes
+    L.EX = direct ? D * R : round_up(D * R, xa);
     L.RH0 = TH + 2 * L.EY;
     L.RW0 = TW + 2 * L.EX;
     // pass H sweeps full SW-wide segments over the widest output region (RW0 - 2R): the
@@ -97,7 +98,7 @@ struct Fwd2Params {
     int D;
     int tiles_x, tiles_y, ntiles;  // tile grid; ntiles = tiles_x * tiles_y * planes
     int ty_off, tx_off;
-    int tx_shift;                  // tiles start at column k * TW - tx_shift (direct float32: (4 - R % 4) % 4)
+    int tx_shift;                  // tiles start at column k * TW - tx_shift (direct: float32 (4 - R % 4) % 4, 16-bit (8 - R % 8) % 8)
     int ty_shift;                  // tiles start at row k * TH - ty_shift
     unsigned int *err;         // device error word (bit 0: a bounded wait gave up)
 };
@@ -181,6 +182,18 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// four floats as four 16-bit storage values (round to nearest even), packed in 8 bytes
+template <typename T> __device__ __forceinline__ uint2 pack4_16(float4 v);
+template <> __device__ __forceinline__ uint2 pack4_16<__half>(float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+}
+template <> __device__ __forceinline__ uint2 pack4_16<__nv_bfloat16>(float4 v) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+}
+template <> __device__ __forceinline__ uint2 pack4_16<float>(float4) { return make_uint2(0u, 0u); }
 
 // storage-type stores of four floats
 template <typename T> __device__ __forceinline__ void cvt_store4(T *p, float4 v);
@@ -317,7 +330,8 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                                         const CUtensorMap *dmap = nullptr) {
     constexpr int P = R + 1;         // ring period (the sweep is fully unrolled, so any period is static)
     constexpr int NS = SW + 2 * R;   // sweep steps of one segment (2R of warm-up)
-    constexpr int SH = (DIRECT && sizeof(T) == 4) ? (4 - R % 4) % 4 : 0;  // tile grid shift
+    // tile grid shift mod 4 (both storage types: (4 - R % 4) % 4 = ((8 - R % 8) % 8) % 4)
+    constexpr int SH = DIRECT ? (4 - R % 4) % 4 : 0;
     constexpr float iq = 1.0f / float((R + 1) * (R + 1));
     constexpr float ih = 1.0f / float((R + 1) * (2 * R + 1));
     const float2 iq2 = make_float2(iq, iq), ih2 = make_float2(ih, ih);
@@ -362,6 +376,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         float4 va = arow[0], vb = brow[0], vu = urow[0];
         float4 na = va, nb = vb, nu4 = vu;
         float o[4];
+        uint2 held = make_uint2(0u, 0u);  // 16-bit DIRECT frames: the first half of a 16-byte store
         uint32_t mw = 0;  // DIRECT maps: selections of the current 4-column group
         // the whole segment is unrolled: ring slots, loads, warm-up and stores are static
 #pragma unroll
@@ -463,7 +478,29 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                         *reinterpret_cast<float4 *>(sbuf + lane * 32 + ((c ^ (lane & 7)) << 2)) = v;
                     } else if (DIRECT) {
                         const int dx = g.fx0 - g.ox + xo - 3;  // first column of the 4-vector
-                        if (row_store && (unsigned)dx < (unsigned)g.lx) cvt_store4<T>(grow + (oo - 3), v);
+                        if constexpr (sizeof(T) == 2) {
+                            // 16-bit frames: frame columns 8k..8k+7 leave as one 16-byte store
+                            // when both 4-vectors are this segment's; the tile origin is
+                            // -(8 - R % 8) % 8 mod 8, so each vector's half is static
+                            constexpr int SH8 = (8 - R % 8) % 8;
+                            // (static once the sweep is unrolled)
+                            const int half = (oo - 3 - SH8) & 7;  // 0: columns 8k.., 4: 8k+4..
+                            const bool lo_full = oo - 4 >= 3 && !(SH > 0 && (oo - 4 < SH || oo - 4 >= SH + SW - 4));
+                            const bool hi_full = oo + 4 < SW && !(SH > 0 && (oo + 4 < SH || oo + 4 >= SH + SW - 4));
+                            const bool pairs = g.oy == 0 && (gpitch & 7) == 0;  // a frame, rows on 16 bytes
+                            if (pairs && half == 0 && hi_full) {
+                                held = pack4_16<T>(v);  // stored with its partner
+                            } else if (pairs && half == 4 && lo_full) {
+                                if (row_store && (unsigned)(dx - 4) < (unsigned)g.lx) {
+                                    const uint2 w = pack4_16<T>(v);
+                                    *reinterpret_cast<uint4 *>(grow + (oo - 7)) = make_uint4(held.x, held.y, w.x, w.y);
+                                }
+                            } else if (row_store && (unsigned)dx < (unsigned)g.lx) {
+                                cvt_store4<T>(grow + (oo - 3), v);
+                            }
+                        } else if (row_store && (unsigned)dx < (unsigned)g.lx) {
+                            cvt_store4<T>(grow + (oo - 3), v);
+                        }
                         if (MAPS) {
                             // the word's first column; a word that starts inside the frame may
                             // spill into the row's padding bytes, never past the row pitch

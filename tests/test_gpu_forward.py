@@ -177,8 +177,13 @@ def test_u8_several_passes():
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dt,name,ulp1", [(torch.float16, "f16", 2.0**-10), (torch.bfloat16, "bf16", 2.0**-7)])
 def test_half_storage(dt, name, ulp1):
-    x = synth.round_to_storage(synth.piecewise_stack(1, 2, 150, 190, seed=21, sigma=0.03), name)
-    for r in (1, 4):
+    # r = 1, 3, 6: tile grids shifted by 7, 5, 2 columns (halo exactly r, boxes on 16
+    # bytes); W = 188 with r = 4, 8 also runs the last pass straight into the output
+    cases = [(synth.round_to_storage(synth.piecewise_stack(1, 2, 150, 190, seed=21, sigma=0.03), name), r)
+             for r in (1, 3, 4, 6)]
+    cases += [(synth.round_to_storage(synth.piecewise_stack(1, 1, 70, 188, seed=22, sigma=0.03), name), r)
+              for r in (4, 8)]
+    for x, r in cases:
         out, maps = gpu_filter(x, r, 6, dtype=dt)
         fast, _ = gpu_filter(x, r, 6, dtype=dt, want_maps=False)
         np.testing.assert_array_equal(fast, out)
@@ -190,7 +195,12 @@ def test_half_storage(dt, name, ulp1):
         frac_equal = np.mean(err == 0)
         print(f"\n{name} r={r}: vs rounded oracle max {err.max():.3g} (equal {frac_equal:.4f}); "
               f"vs FP64 oracle max {np.abs(out - exact).max():.3g} mean {np.abs(out - exact).mean():.3g}")
-        assert frac_equal > 0.99
+        # the kernel forms means as S * RN32(1/n): where the exact mean lies on a midpoint
+        # between two storage values (frequent for quantised inputs) the product may fall on
+        # either side and round one ulp away from the even neighbour the oracle takes --
+        # about 1 % of the pixels at r = 3 (n = 16, 28), none at r = 5; the fused and the
+        # single-pass kernels agree bit for bit there
+        assert frac_equal > 0.985
         assert np.quantile(err, 0.999) <= 2 * ulp1
 
 
