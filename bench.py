@@ -228,10 +228,25 @@ def form_fwd_bwd(dev):
 
     units = N * C * H * W * it
     t_f, t_fb, t_ck = _time(fwd, 20), _time(fwd_bwd, 20), _time(fwd_bwd_ck, 10)
-    return {"workload": "16x3x512x512 float32, r=3, 5 passes, MSE(osbf(noisy), clean)",
-            "fwd_mpix_iter_s": units / t_f / 1e6, "fwd_bwd_mpix_iter_s": units / t_fb / 1e6,
-            "fwd_bwd_checkpointed_k2_mpix_iter_s": units / t_ck / 1e6,
-            "fwd_bwd_time_over_fwd": t_fb / t_f}
+    res = {"workload": "16x3x512x512 float32, r=3, 5 passes, MSE(osbf(noisy), clean)",
+           "fwd_mpix_iter_s": units / t_f / 1e6, "fwd_bwd_mpix_iter_s": units / t_fb / 1e6,
+           "fwd_bwd_checkpointed_k2_mpix_iter_s": units / t_ck / 1e6,
+           "fwd_bwd_time_over_fwd": t_fb / t_f}
+    # the parts at the 4096 x 4096 x 3 size, 10 passes: plain forward, map-writing forward,
+    # backward alone
+    xb = torch.from_numpy(synth.piecewise_stack(1, 3, 4096, 4096, seed=51, sigma=0.05)).to(dev)
+    ob, gb, gib = torch.empty_like(xb), torch.randn_like(xb), torch.empty_like(xb)
+    parts = {}
+    for rr in (3, 8):
+        mb = torch.empty(osbf.maps_shape(xb, rr, 10), dtype=torch.uint8, device=dev)
+        tp = _time(lambda: osbf.filter(xb, rr, 10, out=ob), 5)
+        tm = _time(lambda: osbf.filter(xb, rr, 10, maps=mb, out=ob), 5)
+        tb = _time(lambda: osbf.backward(gb, mb, rr, 10, out=gib), 5)
+        u = xb.numel() * 10 / 1e9
+        parts[f"r{rr}"] = {"fwd_gpix_iter_s": u / tp, "fwd_maps_gpix_iter_s": u / tm, "bwd_gpix_iter_s": u / tb}
+        del mb
+    res["parts_4096x4096x3_10_passes"] = parts
+    return res
 
 
 def form_batched(dev):

@@ -40,14 +40,20 @@ struct Layout2 {
     int in_bytes;  // bytes of one TMA box
     int off_in, off_uf, off_ab, off_ua, off_ub, bytes;  // byte offsets (128-aligned)
     int off_st;  // tensor-store staging: NT/32 buffers of 32 x 32 floats, placed 1024-aligned at run time
+    int off_ms;  // single-pass map staging: NT/32 buffers of 32 rows x kMapPitch bytes
 };
 
 __host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
 
 // direct: a single pass whose results go straight from registers to the destination
 // frame (no U^1 buffer in shared memory)
+// Row pitch (bytes) of a warp's map staging: 32 selections of a row plus the grid shift's
+// offset, 9 words (odd: the row-owner word writes hit distinct banks)
+constexpr int kMapPitch = 36;
+
 template <typename T>
-__host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false, bool tstore = false) {
+__host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false, bool tstore = false,
+                                                bool mstage = false) {
     Layout2 L;
     const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
     L.EY = D * R;
@@ -81,6 +87,8 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     if (D >= 2) off = align128(off + rh1 * L.PU * 4);
     L.off_st = off;
     if (tstore) off = align128(off + 1024 + (NT / 32) * 32 * 32 * 4);  // + slack to reach a 1024-byte boundary
+    L.off_ms = off;
+    if (mstage) off = align128(off + (NT / 32) * 32 * kMapPitch);
     L.bytes = off + 16;  // + mbarrier
     return L;
 }
@@ -327,7 +335,12 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                                         const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
                                         T *__restrict__ gdst, long long gpitch, const Geom2 &g,
                                         uint8_t *__restrict__ mplane, float *__restrict__ sbase = nullptr,
-                                        const CUtensorMap *dmap = nullptr) {
+                                        const CUtensorMap *dmap = nullptr, uint8_t *__restrict__ mbase = nullptr) {
+    // DIRECT maps: a warp's 32 x 32 selections are staged (byte b of a row holds output
+    // b - MO; MO puts every full 4-group of the shifted grid on a word) and written out row
+    // by row after the sweep, one byte per lane: 32 contiguous bytes per store instruction
+    // instead of one 4-byte piece in each of 32 rows
+    constexpr int MO = DIRECT ? (4 - (4 - R % 4) % 4) % 4 : 0;
     constexpr int P = R + 1;         // ring period (the sweep is fully unrolled, so any period is static)
     constexpr int NS = SW + 2 * R;   // sweep steps of one segment (2R of warm-up)
     // tile grid shift mod 4 (both storage types: (4 - R % 4) % 4 = ((8 - R % 8) % 8) % 4)
@@ -342,6 +355,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const int rbk = item % nrb, seg = item / nrb;
         const int yo = rbk * 32 + lane;
         float *sbuf = TSTORE ? sbase + warp * 32 * 32 : nullptr;
+        uint8_t *mst = (MAPS && DIRECT) ? mbase + warp * 32 * kMapPitch : nullptr;
         if (TSTORE) {
             if (lane == 0) bulk_wait_read_all();  // the previous tensor store has read this buffer
             __syncwarp();
@@ -467,10 +481,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                     // neighbouring segment: store them one by one
                     const int dx = g.fx0 - g.ox + xo;
                     if (row_store && (unsigned)dx < (unsigned)g.lx) grow[oo] = from_f<T>(o[slot]);
-                    if (MAPS) {
-                        const int fx = g.fx0 + xo;
-                        if (row_map && (unsigned)fx < (unsigned)g.FW) mplane[(long long)fy * g.MP + fx] = (uint8_t)m;
-                    }
+                    if (MAPS) mst[lane * kMapPitch + oo + MO] = (uint8_t)m;
                 } else if (slot == 3) {
                     const float4 v = make_float4(o[0], o[1], o[2], o[3]);
                     if (TSTORE) {
@@ -501,18 +512,24 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                         } else if (row_store && (unsigned)dx < (unsigned)g.lx) {
                             cvt_store4<T>(grow + (oo - 3), v);
                         }
-                        if (MAPS) {
-                            // the word's first column; a word that starts inside the frame may
-                            // spill into the row's padding bytes, never past the row pitch
-                            const int fx = g.fx0 + xo - 3;
-                            if (row_map && (unsigned)fx < (unsigned)g.FW)
-                                *reinterpret_cast<uint32_t *>(mplane + (long long)fy * g.MP + fx) = mw;
-                        }
+                        if (MAPS) *reinterpret_cast<uint32_t *>(mst + lane * kMapPitch + oo - 3 + MO) = mw;
                     } else if (row_ok) {
                         orow[oo >> 2] = v;
                     }
                 }
             }
+        }
+        if (MAPS && DIRECT) {
+            __syncwarp();
+            const int fx = g.fx0 + xs + lane;  // this lane's frame column
+            if (mplane != nullptr && (unsigned)fx < (unsigned)g.FW) {
+                const int fy0 = g.fy0 + rbk * 32;
+                const int nr = g.RHo - rbk * 32 < 32 ? g.RHo - rbk * 32 : 32;
+                for (int j = 0; j < nr; ++j)
+                    if ((unsigned)(fy0 + j) < (unsigned)g.FH)
+                        mplane[(long long)(fy0 + j) * g.MP + fx] = mst[j * kMapPitch + lane + MO];
+            }
+            __syncwarp();  // the next segment reuses the buffer
         }
         if (TSTORE) {
             // every lane's staged writes become visible to the copy engine, then one lane
@@ -559,7 +576,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 :
     static_assert(!TSTORE || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0), "tensor stores: float32, R % 4 == 0");
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
-    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE);
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT);
     float *sbase = nullptr;  // TSTORE staging, 1024-aligned (the 128-byte swizzle repeats every 1024 bytes)
     if (TSTORE) {
         const uint32_t a = smem_u32(smem2 + L.off_st);
@@ -678,7 +695,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 :
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
             pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g,
-                                                               mplane, sbase, &dmap);
+                                                               mplane, sbase, &dmap, smem2 + L.off_ms);
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
@@ -727,7 +744,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 :
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
 cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream,
                         const CUtensorMap *dmap = nullptr) {
-    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE);
+    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE, MAPS && DIRECT);
     auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
@@ -737,7 +754,7 @@ cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, c
 
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
 int occupancy_fwd2(int D) {
-    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE);
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT);
     auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess) return 0;
     int n = 0;
