@@ -150,11 +150,12 @@ __device__ __forceinline__ void bwd_pass_v(float *__restrict__ gb, const uint8_t
 }
 
 // pass H: lane = tile row, warp = one SW-column segment.  g_in of the tile goes from
-// registers to the outgoing frame; SH realigns the 4-vectors to 16-byte columns.
-template <int R>
+// registers to the outgoing frame (SH realigns the 4-vectors to 16-byte columns), or --
+// STAGE -- stays in `keep` (index = output column in the segment) for a staged write.
+template <int R, bool STAGE>
 __device__ __forceinline__ void bwd_pass_h(const float *__restrict__ gb, const float2 *__restrict__ F12,
                                            const BLayout &L, float *__restrict__ gdst, int pitch, int ty0, int tx0,
-                                           int FH, int FW) {
+                                           int FH, int FW, float (&keep)[SW]) {
     constexpr int P = R + 1;
     constexpr int NS = SW + 2 * R;
     constexpr int SH = (4 - R % 4) % 4;
@@ -195,7 +196,9 @@ __device__ __forceinline__ void bwd_pass_h(const float *__restrict__ gb, const f
             const int oo = t - 2 * R;    // output index within the segment
             const int slot = (oo - SH) & 3;
             o[slot] = h1[sl] + HL.y - r3[sl];
-            if (SH > 0 && (oo < SH || oo >= SH + SW - 4)) {
+            if (STAGE) {
+                keep[oo] = o[slot];
+            } else if (SH > 0 && (oo < SH || oo >= SH + SW - 4)) {
                 const int fx = tx0 + xs + oo;
                 if (row_store && (unsigned)fx < (unsigned)FW) grow[oo] = o[slot];
             } else if (slot == 3) {
@@ -206,6 +209,14 @@ __device__ __forceinline__ void bwd_pass_h(const float *__restrict__ gb, const f
         }
     }
 }
+
+// Staged stores (r <= 4, where the 32 results per lane fit the register budget): after the
+// barrier that ends pass H, each pass-H warp parks its 32 x 32 results in the dead (F1, F2)
+// field (rows of kStagePitch floats, an odd number of 16-byte chunks) and writes them row
+// by row, a lane per column: 32 consecutive floats per store instruction instead of a
+// 16-byte piece in each of 32 rows.
+constexpr int kStagePitch = 36;
+template <int R> __host__ __device__ constexpr bool bwd_stage() { return R <= 4; }
 
 template <int R>
 __global__ void __launch_bounds__(NT, R <= 8 ? 3 : 2)
@@ -277,8 +288,26 @@ __global__ void __launch_bounds__(NT, R <= 8 ? 3 : 2)
         phase ^= 1;
         bwd_pass_v<R>(gb, mb, F12, L);
         __syncthreads();
-        bwd_pass_h<R>(gb, F12, L, p.gdst + (long long)plane * p.dst_plane, p.dst_pitch, ty0, tx0, p.FH, p.FW);
+        float keep[SW];
+        float *gplane = p.gdst + (long long)plane * p.dst_plane;
+        bwd_pass_h<R, bwd_stage<R>()>(gb, F12, L, gplane, p.dst_pitch, ty0, tx0, p.FH, p.FW, keep);
         __syncthreads();
+        if (bwd_stage<R>()) {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (warp < TW / SW) {
+                float *stg = reinterpret_cast<float *>(F12) + warp * 32 * kStagePitch;
+#pragma unroll
+                for (int c = 0; c < SW / 4; ++c)
+                    *reinterpret_cast<float4 *>(stg + lane * kStagePitch + 4 * c) =
+                        make_float4(keep[4 * c], keep[4 * c + 1], keep[4 * c + 2], keep[4 * c + 3]);
+                __syncwarp();
+                const int fx = tx0 + warp * SW + lane;
+                if ((unsigned)fx < (unsigned)p.FW)
+                    for (int j = 0; j < TH; ++j)
+                        if (ty0 + j < p.FH) gplane[(long long)(ty0 + j) * p.dst_pitch + fx] = stg[j * kStagePitch + lane];
+            }
+            // the next tile's pass V writes (F1, F2) after the barrier at the top of the loop
+        }
         const int next = tile + gridDim.x;
         if (next < p.ntiles && threadIdx.x == 0) {  // both boxes are dead: load the next tile
             v2::fence_proxy_async();
