@@ -11,6 +11,9 @@
 
 namespace osbf {
 
+// direct float32 kernels stage their results per warp and write them a row at a time
+template <typename T> constexpr bool kStage = sizeof(T) == 4;
+
 template <typename T, bool APP_MAPS>
 cudaError_t launch_fwd2_t(int R, bool tie_app, bool maps, bool direct, const CUtensorMap &src,
                           const v2::Fwd2Params &p, int grid, cudaStream_t s) {
@@ -18,8 +21,8 @@ cudaError_t launch_fwd2_t(int R, bool tie_app, bool maps, bool direct, const CUt
 #define OSBF_CASE(RR)                                                                                    \
     case RR:                                                                                             \
         if (direct && !tie_app)                                                                          \
-            return maps ? v2::launch_fwd2<T, RR, false, true, true>(src, p, grid, s)                     \
-                        : v2::launch_fwd2<T, RR, false, false, true>(src, p, grid, s);                   \
+            return maps ? v2::launch_fwd2<T, RR, false, true, true, false, false, kStage<T>>(src, p, grid, s) \
+                        : v2::launch_fwd2<T, RR, false, false, true, false, false, kStage<T>>(src, p, grid, s); \
         if (tie_app) {                                                                                   \
             if (!maps) return v2::launch_fwd2<T, RR, true, false, false>(src, p, grid, s);               \
             if constexpr (APP_MAPS) return v2::launch_fwd2<T, RR, true, true, false>(src, p, grid, s);   \
@@ -39,8 +42,8 @@ int occupancy_fwd2_t(int R, bool tie_app, bool maps, bool direct, int D) {
 #define OSBF_CASE(RR)                                                                     \
     case RR:                                                                              \
         if (direct && !tie_app)                                                           \
-            return maps ? v2::occupancy_fwd2<T, RR, false, true, true>(D)                 \
-                        : v2::occupancy_fwd2<T, RR, false, false, true>(D);               \
+            return maps ? v2::occupancy_fwd2<T, RR, false, true, true, false, false, kStage<T>>(D) \
+                        : v2::occupancy_fwd2<T, RR, false, false, true, false, false, kStage<T>>(D); \
         if (tie_app) {                                                                    \
             if (!maps) return v2::occupancy_fwd2<T, RR, true, false, false>(D);           \
             if constexpr (APP_MAPS) return v2::occupancy_fwd2<T, RR, true, true, false>(D); \

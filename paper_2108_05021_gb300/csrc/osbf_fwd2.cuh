@@ -41,6 +41,7 @@ struct Layout2 {
     int off_in, off_uf, off_ab, off_ua, off_ub, bytes;  // byte offsets (128-aligned)
     int off_st;  // tensor-store staging: NT/32 buffers of 32 x 32 floats, placed 1024-aligned at run time
     int off_ms;  // single-pass map staging: NT/32 buffers of 32 rows x kMapPitch bytes
+    int off_xs;  // single-pass result staging: NT/32 buffers of 32 rows x kOutPitch floats
 };
 
 __host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
@@ -50,10 +51,13 @@ __host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
 // Row pitch (bytes) of a warp's map staging: 32 selections of a row plus the grid shift's
 // offset, 9 words (odd: the row-owner word writes hit distinct banks)
 constexpr int kMapPitch = 36;
+// Row pitch (floats) of a warp's result staging (XSTAGE): 9 chunks of 16 bytes (odd: the
+// row-owner 16-byte writes hit distinct banks)
+constexpr int kOutPitch = 36;
 
 template <typename T>
 __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false, bool tstore = false,
-                                                bool mstage = false) {
+                                                bool mstage = false, bool xstage = false) {
     Layout2 L;
     const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
     L.EY = D * R;
@@ -89,6 +93,8 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     if (tstore) off = align128(off + 1024 + (NT / 32) * 32 * 32 * 4);  // + slack to reach a 1024-byte boundary
     L.off_ms = off;
     if (mstage) off = align128(off + (NT / 32) * 32 * kMapPitch);
+    L.off_xs = off;
+    if (xstage) off = align128(off + (NT / 32) * 32 * kOutPitch * 4);
     L.bytes = off + 16;  // + mbarrier
     return L;
 }
@@ -330,12 +336,19 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
 // c ^ (y & 7): the row-owner 4-vectors hit 8 distinct chunks per 8 lanes) and one lane
 // writes it with a tensor store -- the copy engine writes whole lines instead of 32
 // scattered 16-byte pieces per store instruction.
-template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
+template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
+          bool XSTAGE = false>
 __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, int urow0,
                                         const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
                                         T *__restrict__ gdst, long long gpitch, const Geom2 &g,
                                         uint8_t *__restrict__ mplane, float *__restrict__ sbase = nullptr,
-                                        const CUtensorMap *dmap = nullptr, uint8_t *__restrict__ mbase = nullptr) {
+                                        const CUtensorMap *dmap = nullptr, uint8_t *__restrict__ mbase = nullptr,
+                                        float *__restrict__ xbase = nullptr) {
+    // XSTAGE (DIRECT float32): a warp's 32 x 32 results are staged like the selections
+    // (float b of a row holds output b - MO) and written out row by row after the sweep, a
+    // lane per column: 32 consecutive floats per store instruction instead of a 16-byte
+    // piece in each of 32 rows, at any grid shift
+    static_assert(!XSTAGE || (DIRECT && sizeof(T) == 4 && !TSTORE), "result staging: direct float32");
     // DIRECT maps: a warp's 32 x 32 selections are staged (byte b of a row holds output
     // b - MO; MO puts every full 4-group of the shifted grid on a word) and written out row
     // by row after the sweep, one byte per lane: 32 contiguous bytes per store instruction
@@ -356,6 +369,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const int yo = rbk * 32 + lane;
         float *sbuf = TSTORE ? sbase + warp * 32 * 32 : nullptr;
         uint8_t *mst = (MAPS && DIRECT) ? mbase + warp * 32 * kMapPitch : nullptr;
+        float *xst = XSTAGE ? xbase + warp * 32 * kOutPitch : nullptr;
         if (TSTORE) {
             if (lane == 0) bulk_wait_read_all();  // the previous tensor store has read this buffer
             __syncwarp();
@@ -480,7 +494,10 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                     // the segment's first SH and last 4 - SH outputs share a 4-vector with a
                     // neighbouring segment: store them one by one
                     const int dx = g.fx0 - g.ox + xo;
-                    if (row_store && (unsigned)dx < (unsigned)g.lx) grow[oo] = from_f<T>(o[slot]);
+                    if (XSTAGE)
+                        xst[lane * kOutPitch + oo + MO] = o[slot];
+                    else if (row_store && (unsigned)dx < (unsigned)g.lx)
+                        grow[oo] = from_f<T>(o[slot]);
                     if (MAPS) mst[lane * kMapPitch + oo + MO] = (uint8_t)m;
                 } else if (slot == 3) {
                     const float4 v = make_float4(o[0], o[1], o[2], o[3]);
@@ -509,6 +526,8 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                             } else if (row_store && (unsigned)dx < (unsigned)g.lx) {
                                 cvt_store4<T>(grow + (oo - 3), v);
                             }
+                        } else if (XSTAGE) {
+                            *reinterpret_cast<float4 *>(xst + lane * kOutPitch + oo - 3 + MO) = v;
                         } else if (row_store && (unsigned)dx < (unsigned)g.lx) {
                             cvt_store4<T>(grow + (oo - 3), v);
                         }
@@ -518,6 +537,18 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                     }
                 }
             }
+        }
+        if (XSTAGE) {
+            __syncwarp();
+            const int dx = g.fx0 - g.ox + xs + lane;  // this lane's destination column
+            if ((unsigned)dx < (unsigned)g.lx) {
+                const int dy0 = g.fy0 - g.oy + rbk * 32;
+                const int nr = g.RHo - rbk * 32 < 32 ? g.RHo - rbk * 32 : 32;
+                for (int j = 0; j < nr; ++j)
+                    if ((unsigned)(dy0 + j) < (unsigned)g.ly)
+                        gdst[(long long)(dy0 + j) * gpitch + dx] = from_f<T>(xst[j * kOutPitch + lane + MO]);
+            }
+            __syncwarp();  // the next segment reuses the buffer
         }
         if (MAPS && DIRECT) {
             __syncwarp();
@@ -570,13 +601,14 @@ __device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &
 // DIRECT: one pass per launch whose results (and selections, with MAPS) go from
 // registers straight into the destination (D == 1, halo EX == R); otherwise every pass
 // lands in shared memory and the tile interior is copied out at the end.
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
-__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 : 3) : 2)
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
+          bool XSTAGE = false>
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !XSTAGE ? 4 : 3) : 2)
     osbf_fwd2(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dmap, const Fwd2Params p) {
     static_assert(!TSTORE || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0), "tensor stores: float32, R % 4 == 0");
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
-    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT);
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
     float *sbase = nullptr;  // TSTORE staging, 1024-aligned (the 128-byte swizzle repeats every 1024 bytes)
     if (TSTORE) {
         const uint32_t a = smem_u32(smem2 + L.off_st);
@@ -694,8 +726,9 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 :
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE>(Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g,
-                                                               mplane, sbase, &dmap, smem2 + L.off_ms);
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE>(
+                Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane, sbase, &dmap, smem2 + L.off_ms,
+                reinterpret_cast<float *>(smem2 + L.off_xs));
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
@@ -741,21 +774,23 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE ? 4 :
 }
 
 // dmap: the destination's tensor map (read only by TSTORE kernels; any map otherwise)
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
+          bool XSTAGE = false>
 cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream,
                         const CUtensorMap *dmap = nullptr) {
-    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE, MAPS && DIRECT);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE>;
+    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, L.bytes, stream>>>(src, dmap ? *dmap : src, p);
     return cudaGetLastError();
 }
 
-template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false>
+template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
+          bool XSTAGE = false>
 int occupancy_fwd2(int D) {
-    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE>;
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, L.bytes) != cudaSuccess) return 0;
