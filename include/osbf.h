@@ -27,7 +27,9 @@
  *     stream) and is asynchronous unless stated otherwise.
  *   - Errors come back as osbf_status codes; no exception crosses the ABI.  The
  *     text of the last error of a context is returned by osbf_last_error().
- *   - A context is not thread-safe: use one context per host thread.
+ *   - A context is not thread-safe: use one context per host thread.  Its calls share
+ *     its workspaces: calls on different streams must not overlap on the GPU (order
+ *     the streams with events, or use one context per stream).
  *   - Radii 0..OSBF_MAX_RADIUS are supported; larger r gives OSBF_EUNSUPPORTED.
  *     r = 0 or iters = 0 returns the input unchanged (converted to the output
  *     type for 8-bit input).
