@@ -62,3 +62,24 @@ def test_maps_pitch_rounds_frame_width_to_16_bytes(lib):
     for W in (1, 7, 16, 100, 4096):
         for r in (0, 1, 3, 8, 16):
             assert lib.osbf_maps_pitch(W, r) == -(-(W + 2 * r) // 16) * 16
+
+
+def test_binding_has_no_cpu_path():
+    """Every device entry of the binding refuses host tensors (there is no CPU fallback;
+    host buffers go through filter_host, which copies to the device)."""
+    import torch
+
+    from paper_2108_05021_gb300 import osbf
+
+    x = torch.zeros(1, 1, 8, 8)
+    maps = torch.zeros(osbf.maps_shape(x, 1, 1), dtype=torch.uint8)
+    calls = [
+        lambda: osbf.filter(x, 1, 1),
+        lambda: osbf.filter_fast(x, 1, 1),
+        lambda: osbf.filter_gauss(x, 1, 1.0, 1),
+        lambda: osbf.filter3d(torch.zeros(1, 1, 4, 8, 8), 1, 1),
+        lambda: osbf.backward(x, maps, 1, 1),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
