@@ -704,3 +704,26 @@ def test_gauss_constant_interior_and_trivial_cases():
     img = np.random.default_rng(3).random((5, 6))
     np.testing.assert_array_equal(oracle.gauss_filter(img, 0, 3, 1.0)["out"], img)
     np.testing.assert_array_equal(oracle.gauss_filter(img, 2, 0, 1.0)["out"], img)
+
+
+def test_gauss_hint_with_own_maps_changes_nothing():
+    img = synth.piecewise_stack(1, 2, 23, 31, seed=12)[0].astype(np.float64)
+    a = oracle.gauss_filter(img, 3, 3, 1.7, want_maps=True)
+    b = oracle.gauss_filter(img, 3, 3, 1.7, hint=a["maps"], hint_thresh=1e-6)
+    np.testing.assert_array_equal(a["out"], b["out"])
+    assert b["n_hinted"] == 0
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_gauss_patch_gives_the_frame_value(r):
+    """One pass at a frame pixel depends only on the (2r+1)^2 patch around it, zeros
+    outside the frame: the sampled full-size GPU checks rest on this."""
+    img = np.random.default_rng(r).random((13, 17))
+    frame = np.pad(img, r, mode="edge")
+    full = oracle.gauss_iterate_frame(frame, r, 1, 1.3)
+    FH, FW = frame.shape
+    zf = np.pad(frame, r)  # zeros beyond the frame
+    for y in range(FH):
+        for x in range(FW):
+            patch = zf[y:y + 2 * r + 1, x:x + 2 * r + 1]
+            assert oracle.gauss_iterate_frame(patch, r, 1, 1.3)[r, r] == full[y, x]
