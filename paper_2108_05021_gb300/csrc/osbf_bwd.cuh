@@ -321,6 +321,8 @@ template <int R>
 cudaError_t launch_bwd_kernel(const CUtensorMap &gmap, const CUtensorMap &mmap, const BwdParams &p, int grid,
                               cudaStream_t s) {
     const BLayout L = make_blayout(R);
+    // staged results reuse the (F1, F2) field: TW / SW warps x 32 rows x kStagePitch floats
+    if (bwd_stage<R>() && (size_t)TH * L.PF * 8 < (size_t)(TW / SW) * 32 * kStagePitch * 4) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(osbf_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
     osbf_bwd_kernel<R><<<grid, NT, L.bytes, s>>>(gmap, mmap, p);
