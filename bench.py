@@ -18,8 +18,11 @@ Printed JSON line (rank 0):
                of the same image, r = 8) -- a reported baseline, not the target;
   forms        the other forms against the plain one on the same GPU: forward+backward
                (16x3x512^2, r=3, 5 passes), batched (256 images), float16 / bfloat16
-               storage (7680x4320x3, r=4, 30 passes, error against the FP64 oracle on a
-               sampled region), and the r x fused-depth sweep at 4096^2 x 3.
+               storage (7680x4320x3, r=4, 30 passes; distance of the 16-bit results from
+               the float32 results on a sampled region -- the error against the FP64
+               oracle at this configuration is measured by the test suite), the fast
+               approximation, the 3D filter, the one-sided Gaussian filter, and the
+               r x fused-depth sweep at 4096^2 x 3.
 
 `--impl reference` times the CPU oracle as the reference arm (bounded sample per step).
 Multi-GPU: `torchrun --nproc-per-node N bench.py --gpus N`: every rank filters its own
@@ -283,26 +286,31 @@ def form_batched(dev):
 
 
 def form_precision(dev):
-    """7680 x 4320 x 3 stored as f32 / f16 / bf16, r = 4, 30 passes, sigma 0.03."""
+    """7680 x 4320 x 3 stored as f32 / f16 / bf16, r = 4, 30 passes, sigma 0.03: throughput,
+    and the 16-bit results' distance from the float32 results (the error against the FP64
+    oracle at this configuration is measured in tests/test_gpu_forward.py)."""
     import torch
 
-    import oracle
     from paper_2108_05021_gb300 import osbf, synth
 
     H, W, r, it = 4320, 7680, 4, 30
     x32 = synth.piecewise_stack(1, 3, H, W, seed=3, sigma=0.03)
     res = {"workload": "1x3x4320x7680, r=4, 30 passes, sigma 0.03"}
     y0, x0, s = H // 2, W // 2, 48  # sampled output region of plane 0
+    ref = None
     for name, dt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
         xin = x32 if name == "f32" else synth.round_to_storage(x32, name)
         xt = torch.from_numpy(xin).to(dev).to(dt)
         out = torch.empty_like(xt)
         t = _time(lambda: osbf.filter(xt, r, it, out=out), 5)
         got = out[0, 0, y0:y0 + s, x0:x0 + s].float().cpu().numpy()
-        ref = oracle.filter_region(xin[0, 0].astype(np.float64), r, it, y0, y0 + s, x0, x0 + s)
-        err = np.abs(got - ref)
-        res[name] = {"mpix_iter_s": 3 * H * W * it / t / 1e6, "max_abs_err_vs_fp64": float(err.max()),
-                     "mean_abs_err_vs_fp64": float(err.mean()), "err_sample": f"{s}x{s} at ({y0},{x0}), plane 0"}
+        res[name] = {"mpix_iter_s": 3 * H * W * it / t / 1e6}
+        if ref is None:
+            ref = got
+        else:
+            d = np.abs(got - ref)
+            res[name].update({"max_abs_diff_vs_f32": float(d.max()), "mean_abs_diff_vs_f32": float(d.mean()),
+                              "diff_sample": f"{s}x{s} at ({y0},{x0}), plane 0"})
     return res
 
 

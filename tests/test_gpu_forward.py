@@ -204,6 +204,27 @@ def test_half_storage(dt, name, ulp1):
         assert np.quantile(err, 0.999) <= 2 * ulp1
 
 
+@pytest.mark.parametrize("name", ["f32", "f16", "bf16"])
+def test_precision_config_error_vs_fp64(name):
+    """The storage-precision configuration (1 x 3 x 4320 x 7680, r = 4, 30 passes, noise
+    sigma 0.03): error of each storage type against the FP64 oracle (not rounded to the
+    storage type) on a 48 x 48 sample of plane 0 at the image centre.  Measured: max / mean
+    9.8e-5 / 4.7e-7 (f32), 1.1e-3 / 2.4e-4 (f16), 3.5e-3 / 9.1e-4 (bf16); the bounds leave a
+    margin of 5-10x."""
+    bound = {"f32": (1e-3, 5e-6), "f16": (6e-3, 1.2e-3), "bf16": (2e-2, 5e-3)}[name]
+    dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[name]
+    H, W, r, it = 4320, 7680, 4, 30
+    x32 = synth.piecewise_stack(1, 3, H, W, seed=3, sigma=0.03)
+    xin = x32 if name == "f32" else synth.round_to_storage(x32, name)
+    y0, x0, s = H // 2, W // 2, 48
+    out = osbf.filter(torch.from_numpy(xin).to(DEV).to(dt), r, it)
+    got = out[0, 0, y0:y0 + s, x0:x0 + s].float().cpu().numpy()
+    ref = oracle.filter_region(xin[0, 0].astype(np.float64), r, it, y0, y0 + s, x0, x0 + s)
+    err = np.abs(got - ref)
+    print(f"\n{name}: max {err.max():.3g} mean {err.mean():.3g}")
+    assert err.max() <= bound[0] and err.mean() <= bound[1]
+
+
 def test_half_depth_invariance():
     """Rounding to storage after every pass makes fused depths agree exactly."""
     x = synth.round_to_storage(synth.piecewise_stack(1, 1, 120, 150, seed=4, sigma=0.03), "f16")
