@@ -4,9 +4,9 @@ None of these tests compares the oracle with itself.  They check it against
   * a hand-derived worked example (tests/golden/spike_r1.txt);
   * a pure-Python brute force written from the set definitions of Eq. (6)-(13)
     and Algorithm 2 (tiny frames only);
-  * the appendix's construction of the eight difference planes from 1D kernels
-    (k, k_L, k_R) evaluated with scipy's 2D convolution ('same' mode), with the
-    appendix's plane order as tie order;
+  * the eight window means as 2D correlations (scipy) of the padded frame with
+    indicator kernels built from the set definitions of Eq. (6)-(13), in both tie
+    orders;
   * the classical box filter (scipy.ndimage.uniform_filter): half-window and
     quadrant sums must recombine into it (the separable construction of the
     section "Separable Kernels");
@@ -24,7 +24,6 @@ from fractions import Fraction
 import numpy as np
 import pytest
 import scipy.ndimage as ndi
-import scipy.signal as sps
 
 import oracle
 from paper_2108_05021_gb300 import synth
@@ -109,35 +108,44 @@ def test_brute_force_appendix_order():
 
 
 # ----------------------------------------------------------------------------------
-# the appendix's construction: 1D kernels, 2D convolution 'same', min(|d|) first index
+# window means by 2D correlation with the indicator kernels of Eq. (6)-(13)
 # ----------------------------------------------------------------------------------
-def appendix_planes(im, r):
-    """d-planes of the appendix: conv2(col_kernel, row_kernel, im, 'same') - im."""
-    k = np.ones(2 * r + 1) / (2 * r + 1)
-    kl = k.copy()
-    kl[r + 1:] = 0.0
-    kl /= kl.sum()
-    kr = kl[::-1].copy()
-    pairs = [(k, kl), (k, kr), (kl, k), (kr, k), (kl, kl), (kl, kr), (kr, kl), (kr, kr)]
-    return np.stack([sps.convolve2d(im, np.outer(a, b), mode="same") - im for a, b in pairs])
+def window_kernels(r):
+    """The eight box kernels k1..k8 as (2r+1) x (2r+1) weight arrays, each built from the
+    set predicate of its window (Eq. (6)-(13)) and normalised by its pixel count (Sec.
+    "One-sided Kernels for Box Filter").  Entry [dv + r, du + r] weights the pixel at row
+    offset dv and column offset du from the centre."""
+    ks = []
+    for i in range(1, 9):
+        k = np.zeros((2 * r + 1, 2 * r + 1))
+        for dv in range(-r, r + 1):
+            for du in range(-r, r + 1):
+                k[dv + r, du + r] = 1.0 if _in_window(i, r, 0, 0, du, dv) else 0.0
+        ks.append(k / k.sum())
+    return ks
 
 
-def appendix_filter(img, r, iters):
+def correlation_filter(img, r, iters, order):
+    """Algorithm 2 with each window mean taken as a 2D correlation of the frame with its
+    kernel (scipy, zeros beyond the frame), on the replicate-padded frame, first argmin of
+    |d_i| in `order`, cropped at the end."""
     im = np.pad(img, r, mode="edge")
+    ks = window_kernels(r)
     for _ in range(iters):
-        d = appendix_planes(im, r)
-        ind = np.argmin(np.abs(d), axis=0)  # first index wins on ties
-        im = im + np.take_along_axis(d, ind[None], axis=0)[0]
+        means = np.stack([ndi.correlate(im, ks[i - 1], mode="constant", cval=0.0) for i in order])
+        ind = np.argmin(np.abs(means - im), axis=0)  # numpy's argmin returns the first minimum
+        im = np.take_along_axis(means, ind[None], axis=0)[0]
     return im[r:-r or None, r:-r or None] if r else im
 
 
 @pytest.mark.parametrize("r", [1, 2, 3, 5])
-def test_appendix_convolution_semantics(r):
+@pytest.mark.parametrize("tie,order", [("paper", (1, 2, 3, 4, 5, 6, 7, 8)), ("appendix", (6, 5, 7, 8, 2, 1, 3, 4))])
+def test_correlation_semantics(r, tie, order):
     rng = np.random.default_rng(100 + r)
     img = rng.random((17, 23))
     for iters in (1, 3):
-        want = appendix_filter(img, r, iters)
-        got = oracle.filter(img, r, iters, tie="appendix")["out"]
+        want = correlation_filter(img, r, iters, order)
+        got = oracle.filter(img, r, iters, tie=tie)["out"]
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
 
 
@@ -369,6 +377,98 @@ def test_hint_with_own_maps_changes_nothing():
     again = oracle.filter(x, 2, 3, hint=res["maps"], hint_thresh=1e-6)
     np.testing.assert_array_equal(again["out"], res["out"])
     assert again["n_hinted"] == 0
+
+
+def test_hint_threshold_band():
+    """Hinted mode adopts a recorded selection only where its |d| is within hint_thresh of
+    the best |d| (the near-tie band), never elsewhere.
+
+    On the plane u(y, x) = x + 2y the eight means of an interior pixel (windows inside the
+    image) are closed forms: a window spanning column offsets a0..a1 and row offsets b0..b1
+    has mean u + (a0 + a1)/2 + (b0 + b1), so d_1..d_8 = r/2, 3r/2, -r/2, -3r/2, -r/2, r/2,
+    r, -r (Eq. (6)-(13)).  The best |d| = r/2 is shared by N1, N6 (+r/2) and N3, N5 (-r/2);
+    Algorithm 2's first minimum in the paper order is N1, so one pass gives u + r/2."""
+    r, H, W = 3, 20, 26
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = xx + 2 * yy
+    FH, FW = H + 2 * r, W + 2 * r
+    inner = (slice(r, H - r), slice(r, W - r))  # image pixels whose windows stay inside the image
+    n_inner = (H - 2 * r) * (W - 2 * r)
+
+    def run(window, thresh):
+        hint = np.zeros((1, 1, FH, FW), dtype=np.uint8)
+        hint[0, 0, 2 * r:FH - 2 * r, 2 * r:FW - 2 * r] = window  # frame coordinates of the inner pixels
+        return oracle.filter(img, r, 1, hint=hint, hint_thresh=thresh)
+
+    own = oracle.filter(img, r, 1)["out"]
+    np.testing.assert_array_equal(own[inner], img[inner] + r / 2)
+    # outside the band (gap r or r/2 > 1e-6): the oracle keeps its own choice
+    for window in (2, 4, 7, 8):
+        res = run(window, 1e-6)
+        np.testing.assert_array_equal(res["out"], own)
+        assert res["n_hinted"] == 0
+    # inside the band (gap 0): a tied window of the other sign is adopted and counted
+    for window in (3, 5):
+        res = run(window, 1e-6)
+        np.testing.assert_array_equal(res["out"][inner], img[inner] - r / 2)
+        assert res["n_hinted"] == n_inner
+    # a tied window with the same mean changes nothing and is not counted
+    res = run(6, 1e-6)
+    np.testing.assert_array_equal(res["out"], own)
+    assert res["n_hinted"] == 0
+    # the band is strict: with hint_thresh = r, N7 (gap r/2) is adopted, N2 (gap r) is not
+    res = run(7, float(r))
+    np.testing.assert_array_equal(res["out"][inner], img[inner] + r)
+    assert res["n_hinted"] == n_inner
+    res = run(2, float(r))
+    np.testing.assert_array_equal(res["out"], own)
+    assert res["n_hinted"] == 0
+    # the region oracle applies the same band
+    for window, thresh, want in ((3, 1e-6, img - r / 2), (2, 1e-6, img + r / 2), (7, float(r), img + r)):
+        hint = np.zeros((1, FH, FW), dtype=np.uint8)
+        hint[0, 2 * r:FH - 2 * r, 2 * r:FW - 2 * r] = window
+        got, nh = oracle.filter_region(img, r, 1, r, H - r, r, W - r, hint=hint, hint_thresh=thresh,
+                                       return_hinted=True)
+        np.testing.assert_array_equal(got, want[inner])
+        assert nh == (0 if window == 2 else n_inner)
+
+
+def test_hint_threshold_band_fast_and_gauss():
+    """The same band in the fast approximation's and the one-sided Gaussian filter's hinted
+    modes.  On u = x + 2y, Eq. (app) gives the fast variant the exact filter's eight d_i
+    (r/2, 3r/2, -r/2, -3r/2, -r/2, r/2, r, -r); the Gaussian windows give mu, 3mu, -mu,
+    -3mu, -mu, mu, 2mu, -2mu with mu = sum_k w_k k the mean offset of the normalised
+    one-sided Gaussian kernel w_k ~ exp(-k^2 / (2 sigma^2)), k = 0..r."""
+    r, H, W, sigma = 3, 20, 26, 1.5
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = xx + 2 * yy
+    FH, FW = H + 2 * r, W + 2 * r
+    inner = (slice(r, H - r), slice(r, W - r))
+    n_inner = (H - 2 * r) * (W - 2 * r)
+    w = np.exp(-np.arange(r + 1) ** 2 / (2 * sigma**2))
+    mu = float((w * np.arange(r + 1)).sum() / w.sum())
+
+    def hint_of(window):
+        h = np.zeros((1, 1, FH, FW), dtype=np.uint8)
+        h[0, 0, 2 * r:FH - 2 * r, 2 * r:FW - 2 * r] = window
+        return h
+
+    own = oracle.fast_filter(img, r, 1)["out"]
+    np.testing.assert_array_equal(own[inner], img[inner] + r / 2)
+    for window, thresh, want, counted in ((3, 1e-6, img - r / 2, True), (2, 1e-6, own, False),
+                                          (7, float(r), img + r, True), (2, float(r), own, False)):
+        res = oracle.fast_filter(img, r, 1, hint=hint_of(window), hint_thresh=thresh)
+        np.testing.assert_array_equal(res["out"][inner], want[inner])
+        assert res["n_hinted"] == (n_inner if counted else 0)
+
+    own = oracle.gauss_filter(img, r, 1, sigma)["out"]
+    for window, thresh, want in ((3, 1e-6, img - mu), (1, 1e-6, img + mu), (7, 1.5 * mu, img + 2 * mu)):
+        res = oracle.gauss_filter(img, r, 1, sigma, hint=hint_of(window), hint_thresh=thresh)
+        np.testing.assert_allclose(res["out"][inner], want[inner], rtol=0, atol=1e-9)
+    for window, thresh in ((2, 1e-6), (8, 1e-6), (2, 1.5 * mu)):  # gaps 2mu, mu, 2mu: outside the band
+        res = oracle.gauss_filter(img, r, 1, sigma, hint=hint_of(window), hint_thresh=thresh)
+        np.testing.assert_array_equal(res["out"], own)
+        assert res["n_hinted"] == 0
 
 
 def test_storage_rounding_matches_torch():
