@@ -53,7 +53,7 @@ typedef enum {
     OSBF_ENOMEM = 2,       /* a workspace allocation failed */
     OSBF_ECUDA = 3,        /* a CUDA runtime or driver call failed */
     OSBF_EUNSUPPORTED = 4, /* valid but not supported (r > OSBF_MAX_RADIUS, dtype, ...) */
-    OSBF_ETIMEOUT = 5      /* a bounded device-side wait gave up (batched launch) */
+    OSBF_ETIMEOUT = 5      /* a bounded device-side wait gave up (outputs of that call undefined) */
 } osbf_status;
 
 typedef enum {
@@ -274,17 +274,21 @@ int osbf_last_launch_count(const osbf_ctx *ctx);
  * process owns all device memory through its own allocator.
  *   - No context: it runs on the current CUDA device, on `stream`.  The caller passes
  *     device input and output (N x C x H x W float32, not aliasing), as for
- *     osbf_filter(); tie order is the paper's, one pass per launch.
+ *     osbf_filter(); tie order is the paper's, one pass per launch, with the launch plan
+ *     of osbf_filter(): the results equal osbf_filter()'s bit for bit.
  *   - Its scratch is a fixed device array inside the library: two padded frames of at
  *     most OSBF_NOALLOC_MAX_FRAME_FLOATS floats each (N*C*(H+2r) rows of (W+2r) rounded
  *     up to 32 floats); every GPU that loads the library holds this 32 MiB until exit.
  *     Larger problems return OSBF_EUNSUPPORTED, as does r > OSBF_MAX_RADIUS; bad
  *     arguments return OSBF_EINVAL; a failed CUDA call returns OSBF_ECUDA.
+ *   - Synchronous: the call reads the kernels' device error word back and returns once
+ *     `stream` has finished the filter.  OSBF_ETIMEOUT means a bounded tile-load wait
+ *     gave up inside a kernel and the output is undefined.
  *   - The first call on a device looks up the array's device address (once per
  *     device); make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents (each call
- *     rewrites what it reads).  Calls that overlap on the GPU race on it: serialise
- *     them (one stream, or events).
+ *     rewrites what it reads, and clears the error word).  Calls that overlap on the GPU
+ *     race on it: serialise them (one stream, or events).
  */
 #define OSBF_NOALLOC_MAX_FRAME_FLOATS (4LL << 20)
 osbf_status osbf_filter_noalloc(const float *in, float *out, int N, int C, int H, int W, int r, int iters,

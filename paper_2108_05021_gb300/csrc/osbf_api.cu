@@ -136,33 +136,11 @@ int size_class(long long pixels) {
 // ------------------------------------------------------------------------------------
 namespace {
 
-struct V2Plan {
-    int D;
-    size_t smem;
-};
-
 size_t smem_v2(Storage st, int r, int D, bool direct = false) {
     switch (st) {
     case Storage::F16: return smem_fwd2_f16(r, D, direct);
     case Storage::BF16: return smem_fwd2_bf16(r, D, direct);
     default: return smem_fwd2_f32(r, D, direct);
-    }
-}
-
-int occupancy_v2(Storage st, int r, bool tie_app, bool maps, bool direct, int D) {
-    switch (st) {
-    case Storage::F16: return occupancy_fwd2_f16(r, tie_app, maps, direct, D);
-    case Storage::BF16: return occupancy_fwd2_bf16(r, tie_app, maps, direct, D);
-    default: return occupancy_fwd2_f32(r, tie_app, maps, direct, D);
-    }
-}
-
-cudaError_t launch_v2(Storage st, int r, bool tie_app, bool maps, bool direct, const CUtensorMap &m,
-                      const v2::Fwd2Params &p, int grid, cudaStream_t s) {
-    switch (st) {
-    case Storage::F16: return launch_fwd2_f16(r, tie_app, maps, direct, m, p, grid, s);
-    case Storage::BF16: return launch_fwd2_bf16(r, tie_app, maps, direct, m, p, grid, s);
-    default: return launch_fwd2_f32(r, tie_app, maps, direct, m, p, grid, s);
     }
 }
 
@@ -177,6 +155,93 @@ int fit_depth(osbf_ctx *ctx, Storage st, int r, int D) {
 }
 
 }  // namespace
+
+// One launch of the forward: `D` passes from the padded frame `src` into a frame or the
+// caller's cropped output.  Every entry point that runs the float32 / 16-bit forward goes
+// through here, so the choice of kernel variant, tile grid and summation order -- and
+// with it the result, bit for bit -- is the same for all of them.
+cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char **what) {
+    const Storage st = gl.st;
+    const int r = gl.r, Dg = gl.D, P = gl.P, H = gl.H, W = gl.W;
+    const int FH = H + 2 * r, FW = W + 2 * r;
+    *what = "forward launch failed";
+    // one pass written straight from registers into the destination: a frame, or the
+    // cropped output when its rows hold aligned 4-vectors (W % 4 == 0, r % 4 == 0); any r
+    // (the tile grid shifts so the halo stays exactly r columns while the TMA box starts
+    // on 16 bytes)
+    const bool last_out = gl.dst_is_output != 0;
+    const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
+                                      ((uintptr_t)gl.dst % (st == Storage::F32 ? 16 : 8)) == 0);
+    const bool direct = Dg == 1 && gl.tie == 0 && out_ok;
+    // float32 single passes at r % 4 == 0 (no maps) from frame to frame: results leave
+    // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
+    // stores (the last pass, into the cropped output, stages its rows instead, on the
+    // same tile grid, so every call path shares one summation order)
+    const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !gl.maps && !last_out;
+    const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
+                          : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
+                                               : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
+    const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
+    CUtensorMap map;
+    if (!encode_frame_map(&map, st, gl.src, FW, FH, P, gl.src_pitch, L.BX, L.RH0)) {
+        *what = "cuTensorMapEncodeTiled failed (source frame)";
+        return cudaErrorInvalidValue;
+    }
+    v2::Fwd2Params p;
+    std::memset(&p, 0, sizeof p);
+    p.H = H;
+    p.W = W;
+    p.FH = FH;
+    p.FW = FW;
+    p.D = Dg;
+    p.maps = gl.maps;
+    p.map_pitch = maps_pitch(FW);
+    p.map_iter0 = gl.map_iter0;
+    p.map_iter_stride = gl.map_iter_stride;
+    p.map_plane = (long long)FH * p.map_pitch;
+    p.err = gl.err;
+    p.dst = gl.dst;
+    p.dst_is_output = last_out ? 1 : 0;
+    p.dst_pitch = last_out ? W : gl.dst_pitch;
+    p.dst_plane = last_out ? (long long)H * W : (long long)FH * gl.dst_pitch;
+    // tile k spans frame columns [k*TW - shift, (k+1)*TW - shift)
+    int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1 + shift) / v2::TW;
+    if (last_out && !gl.maps) {  // with maps, every frame pixel's selection is recorded
+        ty0 = r / v2::TH;
+        ty1 = (r + H - 1) / v2::TH;
+        tx0 = (r + shift) / v2::TW;
+        tx1 = (r + W - 1 + shift) / v2::TW;
+    }
+    p.ty_off = ty0;
+    p.tx_off = tx0;
+    p.tx_shift = shift;
+    p.tiles_x = tx1 - tx0 + 1;
+    p.tiles_y = ty1 - ty0 + 1;
+    CUtensorMap dmap;
+    if (tstore && !encode_store_map(&dmap, p.dst, FW, FH, P, p.dst_pitch)) {
+        *what = "cuTensorMapEncodeTiled failed (frame store map)";
+        return cudaErrorInvalidValue;
+    }
+    const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
+    if (ntiles > 0x7fffffffLL) {
+        *what = "too many tiles";
+        return cudaErrorInvalidValue;
+    }
+    p.ntiles = (int)ntiles;
+    int occ = tstore ? occupancy_fwd2_tstore(r, false)
+                     : (st == Storage::F16    ? occupancy_fwd2_f16(r, gl.tie != 0, gl.maps != nullptr, direct, Dg)
+                        : st == Storage::BF16 ? occupancy_fwd2_bf16(r, gl.tie != 0, gl.maps != nullptr, direct, Dg)
+                                              : occupancy_fwd2_f32(r, gl.tie != 0, gl.maps != nullptr, direct, Dg));
+    if (occ < 1) occ = 1;
+    const long long g = (long long)occ * gl.sms;
+    const int grid = (int)(g < ntiles ? g : ntiles);
+    if (tstore) return launch_fwd2_tstore(r, false, map, dmap, p, grid, s);
+    switch (st) {
+    case Storage::F16: return launch_fwd2_f16(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
+    case Storage::BF16: return launch_fwd2_bf16(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
+    default: return launch_fwd2_f32(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
+    }
+}
 
 // Runs `iters` passes.  `in` is the caller's image (in_is_frame = 0) or a padded frame
 // of the storage type (in_is_frame = 1, row pitch in_pitch elements); `out` is the
@@ -281,84 +346,38 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     while (passes < iters) {
         const int Dg = iters - passes < D ? iters - passes : D;
         const bool last = passes + Dg == iters;
-        // one pass written straight from registers into the destination: a frame, or the
-        // cropped output when its rows hold aligned 4-vectors (W % 4 == 0, r % 4 == 0); any r
-        // (the tile grid shifts so the halo stays exactly r columns while the TMA box starts
-        // on 16 bytes)
-        const bool last_out = passes + Dg == iters && !out_is_frame;
-        const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
-                                          ((uintptr_t)out % (st == Storage::F32 ? 16 : 8)) == 0);
-        const bool direct = Dg == 1 && tie == 0 && out_ok;
-        // float32 single passes at r % 4 == 0 (no maps) from frame to frame: results leave
-        // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
-        // stores (the last pass, into the cropped output, keeps the register stores and
-        // the same tile grid, so every call path shares one summation order)
-        const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !maps && !last_out;
-        const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
-                              : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
-                                                   : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
-        const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
-        CUtensorMap map;
-        if (!encode_frame_map(&map, st, src, FW, FH, P, src_pitch, L.BX, L.RH0))
-            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame %dx%dx%d, pitch %d)", FW, FH, P,
-                        src_pitch);
-        v2::Fwd2Params p;
-        std::memset(&p, 0, sizeof p);
-        p.H = H;
-        p.W = W;
-        p.FH = FH;
-        p.FW = FW;
-        p.D = Dg;
-        p.maps = maps;
-        p.map_pitch = MP;
-        p.map_iter0 = maps_iter0 + passes;
-        p.map_iter_stride = maps_iter_stride;
-        p.map_plane = (long long)FH * MP;
-        p.err = ctx->err_word;
+        GroupLaunch gl;
+        gl.st = st;
+        gl.r = r;
+        gl.D = Dg;
+        gl.tie = tie;
+        gl.src = src;
+        gl.src_pitch = src_pitch;
+        gl.P = P;
+        gl.H = H;
+        gl.W = W;
+        gl.maps = maps;
+        gl.map_iter0 = maps_iter0 + passes;
+        gl.map_iter_stride = maps_iter_stride;
+        gl.err = ctx->err_word;
+        gl.sms = ctx->sms;
         int nxt = -1;
         if (last && !out_is_frame) {
-            p.dst = out;
-            p.dst_is_output = 1;
-            p.dst_plane = (long long)H * W;
-            p.dst_pitch = W;
+            gl.dst = out;
+            gl.dst_is_output = 1;
         } else if (last) {
-            p.dst = out;
-            p.dst_plane = (long long)FH * out_pitch;
-            p.dst_pitch = out_pitch;
+            gl.dst = out;
+            gl.dst_pitch = out_pitch;
         } else {
             nxt = cur == 0 ? 1 : 0;
             void *f = frame(nxt);
             if (!f) return OSBF_ENOMEM;
-            p.dst = f;
-            p.dst_plane = (long long)FH * FWp;
-            p.dst_pitch = FWp;
+            gl.dst = f;
+            gl.dst_pitch = FWp;
         }
-        // tile k spans frame columns [k*TW - shift, (k+1)*TW - shift)
-        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1 + shift) / v2::TW;
-        if (p.dst_is_output && !maps) {  // with maps, every frame pixel's selection is recorded
-            ty0 = r / v2::TH;
-            ty1 = (r + H - 1) / v2::TH;
-            tx0 = (r + shift) / v2::TW;
-            tx1 = (r + W - 1 + shift) / v2::TW;
-        }
-        p.ty_off = ty0;
-        p.tx_off = tx0;
-        p.tx_shift = shift;
-        p.tiles_x = tx1 - tx0 + 1;
-        p.tiles_y = ty1 - ty0 + 1;
-        CUtensorMap dmap;
-        if (tstore && !encode_store_map(&dmap, p.dst, FW, FH, P, p.dst_pitch))
-            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame store map)");
-        const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
-        if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
-        p.ntiles = (int)ntiles;
-        int occ = tstore ? occupancy_fwd2_tstore(r, false) : occupancy_v2(st, r, tie != 0, maps != nullptr, direct, Dg);
-        if (occ < 1) occ = 1;
-        const long long g = (long long)occ * ctx->sms;
-        const int grid = (int)(g < ntiles ? g : ntiles);
-        cudaError_t e = tstore ? launch_fwd2_tstore(r, false, map, dmap, p, grid, s)
-                               : launch_v2(st, r, tie != 0, maps != nullptr, direct, map, p, grid, s);
-        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "forward launch failed: %s", cudaGetErrorString(e));
+        const char *what = nullptr;
+        cudaError_t e = launch_group(gl, s, &what);
+        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
         ctx->last_launches += 1;
         passes += Dg;
         if (nxt >= 0) {

@@ -325,6 +325,55 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
     m = id[0];
 }
 
+// 16-bit storage: the selection of select2, and the new value as the correctly rounded
+// float32 quotient S_m / n_m of the selected window's sum, which the storage conversion
+// then rounds once more.  For a mean lying exactly on a midpoint between two storage
+// values that quotient is the midpoint itself and the conversion rounds it to even, as
+// rounding the exact mean does; S_m * RN(1/n) alone can land an ulp to either side.
+// The window sums ride through the tournament with their scores; the class of the
+// winner (quadrant or half window) is decided by the last comparison.  The quotient
+// comes from q = S * RN(1/n) and one correction step, q' = q + (S - q n) RN(1/n) with
+// the residual exact in an FMA: Markstein's theorem (P. Markstein, IBM J. Res. Dev. 34,
+// 1990) makes q' the correctly rounded S / n given a correctly rounded reciprocal and
+// q within an ulp.
+template <int R, bool TIE_APP, bool IDX>
+__device__ __forceinline__ void select2_exact(float2 d41, float2 d32, float2 d56, float2 d87, float2 s41,
+                                              float2 s32, float2 s56, float2 s87, float &out, int &m) {
+    constexpr float nq = float((R + 1) * (R + 1)), nh = float((R + 1) * (2 * R + 1));
+    constexpr float iq = 1.0f / nq, ih = 1.0f / nh;
+    const float dv[9] = {0.f, d41.y, d32.y, d32.x, d41.x, d56.x, d56.y, d87.y, d87.x};
+    const float sv[9] = {0.f, s41.y, s32.y, s32.x, s41.x, s56.x, s56.y, s87.y, s87.x};
+    float d[8], sm[8];
+    int id[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        id[k] = tie_window<TIE_APP>(k);
+        d[k] = dv[id[k]];
+        sm[k] = sv[id[k]];
+    }
+    auto pk = [&](int a, int b) {
+        const bool take = fabsf(d[b]) < fabsf(d[a]);  // the lower tie position wins ties
+        d[a] = take ? d[b] : d[a];
+        sm[a] = take ? sm[b] : sm[a];
+        if (IDX) id[a] = take ? id[b] : id[a];
+    };
+    pk(0, 1);
+    pk(2, 3);
+    pk(4, 5);
+    pk(6, 7);
+    pk(0, 2);
+    pk(4, 6);
+    const bool take = fabsf(d[4]) < fabsf(d[0]);
+    const float S = take ? sm[4] : sm[0];
+    m = take ? id[4] : id[0];
+    // tie positions 0..3 hold the quadrants in the paper order, the half windows in the
+    // appendix order
+    const bool quad = TIE_APP ? take : !take;
+    const float n = quad ? nq : nh, ri = quad ? iq : ih;
+    const float q = S * ri;
+    out = fmaf(fmaf(-q, n, S), ri, q);
+}
+
 // Output of pass H: a float buffer in shared memory (the next fused pass reads it), or
 // -- DIRECT -- four results at a time straight into the destination frame in global
 // memory (storage type T, 16- or 8-byte stores, rows and columns outside the frame skipped).
@@ -336,14 +385,16 @@ __device__ __forceinline__ void select2(float2 d41, float2 d32, float2 d56, floa
 // c ^ (y & 7): the row-owner 4-vectors hit 8 distinct chunks per 8 lanes) and one lane
 // writes it with a tensor store -- the copy engine writes whole lines instead of 32
 // scattered 16-byte pieces per store instruction.
+// STREAM (the streaming strip kernel, osbf_strip.cuh): the rows of a, b and U live in
+// ring buffers; the caller passes this lane's row offsets (floats) sa, sb, su instead.
 template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false>
+          bool XSTAGE = false, bool STREAM = false>
 __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, int urow0,
                                         const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
                                         T *__restrict__ gdst, long long gpitch, const Geom2 &g,
                                         uint8_t *__restrict__ mplane, float *__restrict__ sbase = nullptr,
                                         const CUtensorMap *dmap = nullptr, uint8_t *__restrict__ mbase = nullptr,
-                                        float *__restrict__ xbase = nullptr) {
+                                        float *__restrict__ xbase = nullptr, int sa = 0, int sb = 0, int su = 0) {
     // XSTAGE (DIRECT float32): a warp's 32 x 32 results are staged like the selections
     // (float b of a row holds output b - MO) and written out row by row after the sweep, a
     // lane per column: 32 consecutive floats per store instruction instead of a 16-byte
@@ -377,9 +428,10 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         const bool row_ok = yo < g.RHo;
         const int yr = row_ok ? yo : g.RHo - 1;
         const int xs = seg * SW;
-        const float4 *arow = reinterpret_cast<const float4 *>(A + yr * pa + xs);        // a: up column sums
-        const float4 *brow = reinterpret_cast<const float4 *>(A + (yr + R) * pa + xs);  // b: down column sums
-        const float4 *urow = reinterpret_cast<const float4 *>(Uin + (yr + urow0) * pu_in + xs);
+        // a: up column sums, b: down column sums
+        const float4 *arow = reinterpret_cast<const float4 *>(A + (STREAM ? sa : yr * pa) + xs);
+        const float4 *brow = reinterpret_cast<const float4 *>(A + (STREAM ? sb : (yr + R) * pa) + xs);
+        const float4 *urow = reinterpret_cast<const float4 *>(Uin + (STREAM ? su : (yr + urow0) * pu_in) + xs);
         float4 *orow = reinterpret_cast<float4 *>(Uout + yr * pu_out + xs);
         const int fy = g.fy0 + yo;
         // DIRECT: frame row fy lands in row fy - g.oy of the destination (0 for a frame,
@@ -463,6 +515,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                 const float2 d41 = fma2(ABx, iq2, nu);
                 const float2 d32 = fma2(ABL, iq2, nu);  // (N3, N2) = (AL(x+r), BL(x+r))
                 float2 d56, d87;
+                float2 s56 = make_float2(0.f, 0.f), s87 = s56;  // (N5, N6) and (N8, N7) sums
                 if (FAST) {
                     // Eq. (app): d5 = (d4 + d1)/2, d6 = (d3 + d2)/2, d8 = (d4 + d3)/2, d7 = (d1 + d2)/2
                     const float2 h = make_float2(0.5f, 0.5f);
@@ -470,14 +523,18 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                     d87 = mul2(add2(d41, d32), h);
                 } else {
                     const float2 sum = add2(ABx, ABL);
-                    const float2 s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);  // (N8, N7)
-                    const float2 s56 = make_float2(h6[sl], n6);  // N5(x) = N6(x - r) : left half of x
+                    s87 = make_float2(sum.x - ra[sl], sum.y - rb[sl]);  // (N8, N7)
+                    s56 = make_float2(h6[sl], n6);                      // N5(x) = N6(x - r) : left half of x
                     d56 = fma2(s56, ih2, nu);
                     d87 = fma2(s87, ih2, nu);
                 }
                 float outv;
                 int m;
-                select2<R, TIE_APP, MAPS>(d41, d32, d56, d87, ux, outv, m);
+                if constexpr (sizeof(T) == 2 && !FAST) {
+                    select2_exact<R, TIE_APP, MAPS>(d41, d32, d56, d87, ABx, ABL, s56, s87, outv, m);
+                } else {
+                    select2<R, TIE_APP, MAPS>(d41, d32, d56, d87, ux, outv, m);
+                }
                 const int xo = xs + t - 2 * R;
                 const int oo = t - 2 * R;  // output index within the segment
                 // column of output oo is congruent to oo - SH mod 4 (SH: the grid shift)

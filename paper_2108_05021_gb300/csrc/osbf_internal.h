@@ -57,6 +57,25 @@ bool encode_frame_map(CUtensorMap *map, Storage st, const void *base, int FW, in
 cudaError_t launch_pad_replicate(Storage st, const void *in, void *frame, int P, int H, int W, int R, int FH, int FW,
                                  int FWp, cudaStream_t s);
 
+// One launch of the forward (D fused passes) from a padded frame into a frame or the
+// caller's cropped output, with the kernel variant every entry point uses (osbf_api.cu).
+struct GroupLaunch {
+    Storage st = Storage::F32;
+    int r = 0, D = 1, tie = 0;
+    const void *src = nullptr;  // padded frame, row pitch src_pitch elements
+    int src_pitch = 0;
+    void *dst = nullptr;  // frame (row pitch dst_pitch) or, with dst_is_output, the H x W output
+    int dst_pitch = 0;
+    int dst_is_output = 0;
+    int P = 0, H = 0, W = 0;
+    uint8_t *maps = nullptr;  // optional selection maps (osbf_filter_ex layout)
+    int map_iter0 = 0;
+    long long map_iter_stride = 0;
+    unsigned int *err = nullptr;  // device error word
+    int sms = 0;
+};
+cudaError_t launch_group(const GroupLaunch &g, cudaStream_t s, const char **what);
+
 // the final crop of a float32 frame into H x W planes (osbf_misc.cu)
 cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W, int R, int FWp, cudaStream_t s);
 

@@ -6,7 +6,8 @@
 // another allocator.  For them this entry point keeps its scratch -- the two padded
 // frames the passes ping-pong between -- in a file-scope device array of fixed size,
 // which every GPU that loads the library holds until the process exits.  It launches
-// the library's existing pad and forward kernels; it needs no context.
+// the library's pad and forward kernels with osbf_filter()'s launch plan; it needs no
+// context.
 #include <cstring>
 #include <mutex>
 
@@ -86,48 +87,35 @@ extern "C" osbf_status osbf_filter_noalloc(const float *in, float *out, int N, i
     if (cudaMemsetAsync(d->err, 0, sizeof(unsigned int), s) != cudaSuccess) return OSBF_ECUDA;
     if (launch_pad_replicate(Storage::F32, in, frame[0], (int)P, H, W, r, FH, FW, FWp, s) != cudaSuccess)
         return OSBF_ECUDA;
-    // one pass per launch from frame to frame; the last pass writes the cropped output
-    const v2::Layout2 L = v2::make_layout2<float>(r, 1);
+    // one pass per launch, frame to frame, the last pass into the cropped output: the launch
+    // plan of osbf_filter(), so both give the same result bit for bit
     int cur = 0;
     for (int pass = 0; pass < iters; ++pass) {
         const bool last = pass == iters - 1;
-        CUtensorMap map;
-        if (!encode_frame_map(&map, Storage::F32, frame[cur], FW, FH, (int)P, FWp, L.BX, L.RH0)) return OSBF_ECUDA;
-        v2::Fwd2Params p;
-        memset(&p, 0, sizeof p);
-        p.H = H;
-        p.W = W;
-        p.FH = FH;
-        p.FW = FW;
-        p.D = 1;
-        p.err = d->err;
-        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1) / v2::TW;
-        if (last) {
-            p.dst = out;
-            p.dst_is_output = 1;
-            p.dst_plane = (long long)H * W;
-            p.dst_pitch = W;
-            ty0 = r / v2::TH;
-            ty1 = (r + H - 1) / v2::TH;
-            tx0 = r / v2::TW;
-            tx1 = (r + W - 1) / v2::TW;
-        } else {
-            p.dst = frame[1 - cur];
-            p.dst_plane = (long long)FH * FWp;
-            p.dst_pitch = FWp;
-        }
-        p.ty_off = ty0;
-        p.tx_off = tx0;
-        p.tiles_x = tx1 - tx0 + 1;
-        p.tiles_y = ty1 - ty0 + 1;
-        p.ntiles = (int)((long long)p.tiles_x * p.tiles_y * P);
-        const bool direct = !last && L.EX == r;
-        int occ = occupancy_fwd2_f32(r, false, false, direct, 1);
-        if (occ < 1) occ = 1;
-        const long long g = (long long)occ * d->sms;
-        if (launch_fwd2_f32(r, false, false, direct, map, p, (int)(g < p.ntiles ? g : p.ntiles), s) != cudaSuccess)
-            return OSBF_ECUDA;
+        GroupLaunch gl;
+        gl.st = Storage::F32;
+        gl.r = r;
+        gl.D = 1;
+        gl.src = frame[cur];
+        gl.src_pitch = FWp;
+        gl.P = (int)P;
+        gl.H = H;
+        gl.W = W;
+        gl.err = d->err;
+        gl.sms = d->sms;
+        gl.dst = last ? (void *)out : (void *)frame[1 - cur];
+        gl.dst_pitch = FWp;
+        gl.dst_is_output = last ? 1 : 0;
+        const char *what = nullptr;
+        if (launch_group(gl, s, &what) != cudaSuccess) return OSBF_ECUDA;
         if (!last) cur = 1 - cur;
     }
+    // a bounded tile-load wait that gave up leaves its tile unwritten: read the device error
+    // word back (the call returns once the stream has finished the filter)
+    unsigned int word = 0;
+    if (cudaMemcpyAsync(&word, d->err, sizeof word, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return OSBF_ECUDA;
+    if (word) return OSBF_ETIMEOUT;
     return OSBF_OK;
 }

@@ -32,11 +32,25 @@ def gpu_filter(x_np, r, iters, depth=0, tie="paper", want_maps=True, dtype=torch
     return out.float().cpu().numpy(), (osbf.maps_frames(maps, x.shape[-1], r).cpu().numpy() if want_maps else None)
 
 
-def check_f32(x_np, r, iters, depth=0, tie="paper"):
+# Hinted pixels: (pixel, pass) pairs where the oracle adopted the GPU's selection inside the
+# near-tie band and that changed the value.  Measured on the noisy float inputs: up to
+# ~2e-5 of all pixel-passes over a few passes, up to ~1.1e-3 after 30 passes (smoothed
+# regions make several windows' means nearly equal).  The bound is 5e-3.
+MAX_HINTED_FRAC = 5e-3
+
+
+def check_f32(x_np, r, iters, depth=0, tie="paper", max_hinted_frac=MAX_HINTED_FRAC):
     out, maps = gpu_filter(x_np, r, iters, depth=depth, tie=tie)
-    ref = oracle.filter(x_np.astype(np.float64), r, iters, tie=tie, hint=maps, hint_thresh=TIE_THRESH)
+    ref = oracle.filter(x_np.astype(np.float64), r, iters, tie=tie, hint=maps, hint_thresh=TIE_THRESH,
+                        want_gaps=True)
     err = np.abs(out.astype(np.float64) - ref["out"])
     assert err.max() <= F32_TOL, (err.max(), np.unravel_index(err.argmax(), err.shape), ref["n_hinted"])
+    frame_px_passes = maps.size
+    assert ref["n_hinted"] <= max(4, max_hinted_frac * frame_px_passes), (ref["n_hinted"], frame_px_passes)
+    # the literal rule's count: output pixels whose last pass had its best two |d_i| within 1e-6
+    literal = int((oracle.crop(ref["gaps"][-1], r) < TIE_THRESH).sum()) if iters > 0 and r > 0 else 0
+    print(f"\n{x_np.shape} r={r} passes={iters}: max|d| {err.max():.3g}, hinted {ref['n_hinted']} of "
+          f"{frame_px_passes} pixel-passes, near ties in the last pass {literal}")
     return out, maps, ref
 
 
@@ -72,6 +86,59 @@ def test_radii_ragged_tiles(shape, r):
     check_f32(x, r, 3)
 
 
+@pytest.mark.parametrize("r", [4, 8, 12, 16])
+@pytest.mark.parametrize("W", [256, 258])
+def test_no_maps_kernels_match_oracle(r, W):
+    """The kernels a plain call runs (no maps): frame-to-frame passes at r % 4 == 0 leave
+    through per-warp tensor stores; the last pass writes the cropped output straight from
+    the kernel when W % 4 == 0 (staged rows) and through the shared-memory kernel otherwise.
+    Their results equal the map-writing run bit for bit (same arithmetic, so the maps run's
+    selections are the no-maps run's), and the oracle, hinted with those maps, agrees
+    within 1e-5 on every pixel."""
+    x = synth.piecewise_stack(1, 2, 97, W, seed=60 + r, sigma=0.05)
+    plain, _ = gpu_filter(x, r, 4, want_maps=False)
+    out, maps, ref = check_f32(x, r, 4)
+    np.testing.assert_array_equal(plain, out)
+    assert np.abs(plain.astype(np.float64) - ref["out"]).max() <= F32_TOL
+
+
+def test_bench_shape_sampled():
+    """The benchmark's own workload and launch sequence: 1 x 3 x 4096 x 4096 float32, r = 8,
+    30 passes, the bench's input (seed 0).  The plain call (tensor-store passes, staged last
+    pass) equals the map-writing call bit for bit on the whole output; 32 x 32 regions --
+    the top-left frame corner, a region straddling a tile seam in both axes, an interior
+    region and the bottom-right corner -- match the oracle (dependency cone only, hinted
+    with the run's maps) within 1e-5."""
+    r, it, H, W = 8, 30, 4096, 4096
+    x_np = synth.piecewise_stack(1, 3, H, W, seed=0, sigma=0.05)
+    x = torch.from_numpy(x_np).to(DEV)
+    plain = osbf.filter(x, r, it)
+    maps = torch.empty(osbf.maps_shape(x, r, it), dtype=torch.uint8, device=DEV)
+    withmaps = osbf.filter(x, r, it, maps=maps)
+    torch.cuda.synchronize()
+    assert torch.equal(plain, withmaps)
+    FH, FW = H + 2 * r, W + 2 * r
+    m = it * r
+    # tiles are 32 rows x 128 columns of the frame: image row 24 and column 120 lie on seams
+    regions = [(0, 0, 0), (0, 8, 104), (1, 2000, 3000), (2, H - 32, W - 32)]
+    total_hinted = 0
+    for p, y0, x0 in regions:
+        y1, x1 = y0 + 32, x0 + 32
+        fy0, fy1 = max(0, y0 + r - m), min(FH, y1 + r + m)
+        fx0, fx1 = max(0, x0 + r - m), min(FW, x1 + r + m)
+        hint = np.zeros((it, FH, FW), dtype=np.uint8)  # pages outside the cone stay untouched
+        hint[:, fy0:fy1, fx0:fx1] = maps[:, p, fy0:fy1, fx0:fx1].cpu().numpy()
+        ref, nh = oracle.filter_region(x_np[0, p].astype(np.float64), r, it, y0, y1, x0, x1, hint=hint,
+                                       hint_thresh=TIE_THRESH, return_hinted=True)
+        got = plain[0, p, y0:y1, x0:x1].cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref).max()
+        print(f"\nplane {p} region ({y0}, {x0}): max|d| {err:.3g}, hinted {nh}")
+        assert err <= F32_TOL
+        total_hinted += nh
+        # the oracle iterates the whole cone: (fy1 - fy0) x (fx1 - fx0) pixels, 30 passes
+        assert nh <= MAX_HINTED_FRAC * (fy1 - fy0) * (fx1 - fx0) * it
+
+
 @pytest.mark.parametrize("depth", [1, 2, 3, 4, 8])
 def test_fused_depths(depth):
     x = synth.piecewise_stack(1, 1, 97, 260, seed=42, sigma=0.05)
@@ -105,8 +172,10 @@ def test_depth_invariance():
 @pytest.mark.parametrize("shape", [(1, 1, 1, 1), (1, 1, 1, 37), (1, 1, 29, 1), (1, 1, 5, 7), (1, 3, 33, 129)])
 @pytest.mark.parametrize("r", [1, 2, 16])
 def test_small_and_degenerate_shapes(shape, r):
+    # frames one pixel wide or high are symmetric (replicated rows or columns), so opposite
+    # windows tie often: measured up to 1.6 % hinted pixel-passes, bound 5 %
     x = synth.piecewise_stack(*shape, seed=7, sigma=0.1)
-    check_f32(x, r, 3)
+    check_f32(x, r, 3, max_hinted_frac=0.05)
 
 
 def test_r0_and_iters0_are_identity():
@@ -122,8 +191,10 @@ def test_tie_order_appendix():
     x = np.round(synth.piecewise_stack(1, 1, 90, 140, seed=8, sigma=0.05) * 16) / 16  # many exact ties
     x = x.astype(np.float32)
     for r in (1, 2, 3):
-        check_f32(x, r, 4, tie="appendix")
-        check_f32(x, r, 4, tie="paper")
+        # values on a 1/16 grid tie exactly between quadrants and half windows, whose means
+        # float32 rounds differently: in-band hints are frequent here (bound 5 %)
+        check_f32(x, r, 4, tie="appendix", max_hinted_frac=0.05)
+        check_f32(x, r, 4, tie="paper", max_hinted_frac=0.05)
 
 
 def test_edges_corners_checkerboard_preserved():
@@ -193,36 +264,68 @@ def test_half_storage(dt, name, ulp1):
         exact = oracle.filter(x.astype(np.float64), r, 6)["out"]
         err = np.abs(out - ref)
         frac_equal = np.mean(err == 0)
-        print(f"\n{name} r={r}: vs rounded oracle max {err.max():.3g} (equal {frac_equal:.4f}); "
-              f"vs FP64 oracle max {np.abs(out - exact).max():.3g} mean {np.abs(out - exact).mean():.3g}")
-        # the kernel forms means as S * RN32(1/n): where the exact mean lies on a midpoint
-        # between two storage values (frequent for quantised inputs) the product may fall on
-        # either side and round one ulp away from the even neighbour the oracle takes --
-        # about 1 % of the pixels at r = 3 (n = 16, 28), none at r = 5; the fused and the
-        # single-pass kernels agree bit for bit there
-        assert frac_equal > 0.985
-        assert np.quantile(err, 0.999) <= 2 * ulp1
+        print(f"\n{name} r={r}: vs rounded oracle max {err.max():.3g} (equal {frac_equal:.5f}, "
+              f"> 1 ulp at 1.0: {(err > ulp1).sum()}); vs FP64 oracle max {np.abs(out - exact).max():.3g} "
+              f"mean {np.abs(out - exact).mean():.3g}")
+        # the kernel's new value is the storage rounding of the correctly rounded float32
+        # quotient S_m / n_m, so it equals the oracle's rounding of the exact mean wherever
+        # the float32 window sums are exact (16-bit values near 1 sum exactly; values below
+        # about 2^-7 carry bits past float32's 24 when summed with large ones)
+        assert frac_equal >= 0.99
+        assert err.max() <= 2 * ulp1
 
 
 @pytest.mark.parametrize("name", ["f32", "f16", "bf16"])
 def test_precision_config_error_vs_fp64(name):
     """The storage-precision configuration (1 x 3 x 4320 x 7680, r = 4, 30 passes, noise
-    sigma 0.03): error of each storage type against the FP64 oracle (not rounded to the
-    storage type) on a 48 x 48 sample of plane 0 at the image centre.  Measured: max / mean
-    9.8e-5 / 4.7e-7 (f32), 1.1e-3 / 2.4e-4 (f16), 3.5e-3 / 9.1e-4 (bf16); the bounds leave a
-    margin of 5-10x."""
-    bound = {"f32": (1e-3, 5e-6), "f16": (6e-3, 1.2e-3), "bf16": (2e-2, 5e-3)}[name]
+    sigma 0.03) on a 48 x 48 sample of plane 0 at the image centre.
+
+    float32: the FP32 rule -- max |delta| <= 1e-5 against the FP64 oracle hinted with the
+    run's own maps (near ties counted).  16-bit storage: the error against the FP64 oracle
+    (not rounded to storage) is reported and bounded with a margin over the measured values
+    (max / mean 1.1e-3 / 2.4e-4 for f16, 3.5e-3 / 9.1e-4 for bf16), and the selection flips
+    against the float32 run -- (frame pixel, pass) pairs whose selected window differs --
+    are counted over all three planes and 30 passes."""
     dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[name]
     H, W, r, it = 4320, 7680, 4, 30
     x32 = synth.piecewise_stack(1, 3, H, W, seed=3, sigma=0.03)
     xin = x32 if name == "f32" else synth.round_to_storage(x32, name)
     y0, x0, s = H // 2, W // 2, 48
-    out = osbf.filter(torch.from_numpy(xin).to(DEV).to(dt), r, it)
-    got = out[0, 0, y0:y0 + s, x0:x0 + s].float().cpu().numpy()
-    ref = oracle.filter_region(xin[0, 0].astype(np.float64), r, it, y0, y0 + s, x0, x0 + s)
-    err = np.abs(got - ref)
-    print(f"\n{name}: max {err.max():.3g} mean {err.mean():.3g}")
-    assert err.max() <= bound[0] and err.mean() <= bound[1]
+    xt = torch.from_numpy(xin).to(DEV).to(dt)
+    maps = torch.empty(osbf.maps_shape(xt, r, it), dtype=torch.uint8, device=DEV)
+    out = osbf.filter(xt, r, it, maps=maps)
+    got = out[0, 0, y0:y0 + s, x0:x0 + s].float().cpu().numpy().astype(np.float64)
+    plain = oracle.filter_region(xin[0, 0].astype(np.float64), r, it, y0, y0 + s, x0, x0 + s)
+    err_plain = np.abs(got - plain)
+    FH, FW = H + 2 * r, W + 2 * r
+    if name == "f32":
+        m = it * r
+        fy0, fy1, fx0, fx1 = y0 + r - m, y0 + s + r + m, x0 + r - m, x0 + s + r + m
+        hint = np.zeros((it, FH, FW), dtype=np.uint8)
+        hint[:, fy0:fy1, fx0:fx1] = maps[:, 0, fy0:fy1, fx0:fx1].cpu().numpy()
+        ref, nh = oracle.filter_region(xin[0, 0].astype(np.float64), r, it, y0, y0 + s, x0, x0 + s, hint=hint,
+                                       hint_thresh=TIE_THRESH, return_hinted=True)
+        err = np.abs(got - ref)
+        print(f"\nf32: hinted max {err.max():.3g} ({nh} hinted); unhinted max {err_plain.max():.3g} "
+              f"mean {err_plain.mean():.3g}")
+        assert err.max() <= F32_TOL
+        assert nh <= MAX_HINTED_FRAC * (fy1 - fy0) * (fx1 - fx0) * it
+        return
+    bound = {"f16": (6e-3, 1.2e-3), "bf16": (2e-2, 5e-3)}[name]
+    x_f32 = torch.from_numpy(x32).to(DEV)
+    maps32 = torch.empty(osbf.maps_shape(x_f32, r, it), dtype=torch.uint8, device=DEV)
+    osbf.filter(x_f32, r, it, maps=maps32)
+    flips = [int((maps[t, ..., :FW] != maps32[t, ..., :FW]).sum()) for t in range(it)]
+    total = 3 * FH * FW * it
+    print(f"\n{name}: max {err_plain.max():.3g} mean {err_plain.mean():.3g} vs FP64; selection flips vs f32 "
+          f"{sum(flips)} of {total} pixel-passes ({sum(flips) / total:.3%}); pass 1: {flips[0]}, pass 30: "
+          f"{flips[-1]}")
+    assert err_plain.max() <= bound[0] and err_plain.mean() <= bound[1]
+    # Reported, not bounded tightly: the rounded input already changes the first pass's
+    # choice where windows are close (measured 1.0 % f16, 6.5 % bf16 of pass-1 pixels), and
+    # as passes flatten the image, windows with nearly equal means swap freely (25 % / 43 %
+    # of all pixel-passes) at little cost in value (the error bounds above).
+    assert flips[0] < 0.1 * total / it
 
 
 def test_half_depth_invariance():
