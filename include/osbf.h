@@ -76,8 +76,18 @@ typedef struct {
                         osbf_maps_pitch(W, r) bytes, 16-byte aligned: the selected window
                         index (1..8 = N1..N8) of every frame pixel and pass in the first
                         W+2r bytes of each row (the rest of the row is unspecified) */
-    int reserved[4]; /* must be zero */
+    int variant;     /* forward kernel (osbf_variant); 0 = the library's choice */
+    int reserved[3]; /* must be zero */
 } osbf_options;
+
+/* Forward kernels of the float32 single-pass launches (paper tie order).  Both compute the
+ * same filter; they differ in the last bits of the running sums, so a call runs all its
+ * passes with one of them.  OSBF_VARIANT_STRIP covers r <= 8 (OSBF_EUNSUPPORTED above). */
+typedef enum {
+    OSBF_VARIANT_AUTO = 0,  /* the tuned choice (osbf_autotune), else the tile kernel */
+    OSBF_VARIANT_TILE = 1,  /* 32 x 128 tiles, each loaded with its halo by one tensor copy */
+    OSBF_VARIANT_STRIP = 2  /* column strips streamed top to bottom in 32-row chunks, copies a chunk ahead */
+} osbf_variant;
 
 /* Create a context on CUDA device `device`.  *out receives it.  The context owns
  * workspaces (two padded frames per shape class, grown on demand), the tuned

@@ -11,6 +11,7 @@
 
 #include "osbf.h"
 #include "osbf_internal.h"
+#include "osbf_strip.cuh"
 
 using namespace osbf;
 
@@ -32,6 +33,7 @@ struct osbf_ctx {
     void *batch_state = nullptr;                     // owned by the batched launcher
     unsigned int *err_word = nullptr;                // device: bit 0 = a bounded device wait gave up
     unsigned long long wait_ns = 0;                  // bound of the batched dependency wait (0 = default)
+    int call_variant = 0;                            // forward kernel of the current call (osbf_variant)
 };
 
 // implemented in osbf_bwd_api.cu / osbf_batched.cu
@@ -156,6 +158,85 @@ int fit_depth(osbf_ctx *ctx, Storage st, int r, int D) {
 
 }  // namespace
 
+namespace {
+
+// One pass of the streaming strip kernel.  Strips use the tile kernel's column grid (the
+// same shift); each strip's chunk rows are cut into segments so that the segments fill
+// the grid in as few rounds as possible (a segment's start costs a pass-V warm-up of 2r
+// rows and the first copy's latency, about one chunk).
+cudaError_t launch_strip_group(const GroupLaunch &gl, int shift, cudaStream_t s, const char **what) {
+    const int r = gl.r, P = gl.P, H = gl.H, W = gl.W;
+    const int FH = H + 2 * r, FW = W + 2 * r;
+    const bool last_out = gl.dst_is_output != 0;
+    // 32-byte register stores where every strip's destination columns start on 32 bytes:
+    // frames at r % 4 == 0 (no grid shift, pitch a multiple of 32 floats); the cropped
+    // output at r % 8 == 0 with W % 8 == 0 and a 32-byte aligned base
+    const bool v8 = !gl.maps && r % 4 == 0 &&
+                    (!last_out || (r % 8 == 0 && W % 8 == 0 && ((uintptr_t)gl.dst & 31) == 0));
+    strip::StripParams sp;
+    std::memset(&sp, 0, sizeof sp);
+    v2::Fwd2Params &p = sp.f;
+    p.H = H;
+    p.W = W;
+    p.FH = FH;
+    p.FW = FW;
+    p.D = 1;
+    p.maps = gl.maps;
+    p.map_pitch = maps_pitch(FW);
+    p.map_iter0 = gl.map_iter0;
+    p.map_iter_stride = gl.map_iter_stride;
+    p.map_plane = (long long)FH * p.map_pitch;
+    p.err = gl.err;
+    p.dst = gl.dst;
+    p.dst_is_output = last_out ? 1 : 0;
+    p.dst_pitch = last_out ? W : gl.dst_pitch;
+    p.dst_plane = last_out ? (long long)H * W : (long long)FH * gl.dst_pitch;
+    p.tx_shift = shift;
+    // Every launch covers the whole frame with the same segments (the pass into the
+    // cropped output clips its stores): the running sums re-form on the segment's row
+    // phase, so with identical segments the map-writing, the plain and the output-writing
+    // kernels compute every pixel identically.  The plan assumes three CTAs per SM (the
+    // register-store kernels' occupancy) whatever the variant's, for the same reason.
+    sp.ys = 0;
+    sp.nchunks = (FH + strip::CH - 1) / strip::CH;
+    sp.strips_x = (FW - 1 + shift) / v2::TW + 1;
+    sp.tx_off = 0;
+    int occ = occupancy_fwd_strip(r, gl.maps != nullptr, v8);
+    if (occ < 1) occ = 1;
+    const long long G = 3LL * gl.sms;
+    const long long units = (long long)P * sp.strips_x;
+    const double warm = 1.0 + 3.0 * r / strip::CH;  // chunk-equivalents per segment start
+    double best = 1e300;
+    for (int S = 1; S <= 64 && S <= sp.nchunks; ++S) {
+        const int cps = (sp.nchunks + S - 1) / S;
+        const int spp = (sp.nchunks + cps - 1) / cps;
+        const long long nsegs = units * spp;
+        const double cost = (double)((nsegs + G - 1) / G) * (cps + warm);
+        if (cost < best - 1e-9) {
+            best = cost;
+            sp.cps = cps;
+            sp.segs_per_strip = spp;
+        }
+    }
+    const long long nsegs = units * sp.segs_per_strip;
+    if (nsegs > 0x7fffffffLL) {
+        *what = "too many segments";
+        return cudaErrorInvalidValue;
+    }
+    sp.nsegs = (int)nsegs;
+    CUtensorMap map;
+    if (!encode_frame_map(&map, Storage::F32, gl.src, FW, FH, P, gl.src_pitch, strip_box_width(r), strip::BOXH)) {
+        *what = "cuTensorMapEncodeTiled failed (source frame, strip boxes)";
+        return cudaErrorInvalidValue;
+    }
+    const long long Gocc = (long long)occ * gl.sms;
+    const int grid = (int)(Gocc < nsegs ? Gocc : nsegs);
+    *what = "strip forward launch failed";
+    return launch_fwd_strip(r, gl.maps != nullptr, v8, map, sp, grid, s);
+}
+
+}  // namespace
+
 // One launch of the forward: `D` passes from the padded frame `src` into a frame or the
 // caller's cropped output.  Every entry point that runs the float32 / 16-bit forward goes
 // through here, so the choice of kernel variant, tile grid and summation order -- and
@@ -177,13 +258,43 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
     // stores (the last pass, into the cropped output, stages its rows instead, on the
     // same tile grid, so every call path shares one summation order)
-    const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !gl.maps && !last_out;
+    // float32 single passes at r % 4 == 0 of the paper tie order (no maps): results leave by
+    // per-warp tensor stores -- into the next frame, or into the cropped output when its
+    // rows hold whole 16-byte groups (W % 4 == 0, 16-byte aligned base)
+    const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !gl.maps;
+    // The pass into the cropped output runs on the tile grid shifted by (r, r): tiles then
+    // start at output rows 32k and columns 128k, so every tensor store starts at a
+    // non-negative, 16-byte aligned output coordinate.  With maps the same grid, extended
+    // by one tile row and column before the output, also covers the frame ring: the plain
+    // and the map-writing passes share tile origins (and so their running sums' phases).
+    const bool out_grid = last_out && direct && st == Storage::F32 && r % 4 == 0;
+    const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
+    // the streaming strip kernel: float32 single passes of the paper tie order at r <= 8; it
+    // writes the cropped output through staged rows (one float per lane), so any W works
+    const bool strip_ok = Dg == 1 && gl.tie == 0 && st == Storage::F32 && r <= OSBF_STRIP_MAX_R;
+    // (opt-in: on GB300 it runs more instructions than the tile kernel -- its pass V works in
+    // runtime loops of r+1-row periods over ring buffers -- and is slower at every radius)
+    if (strip_ok && gl.variant == 2) return launch_strip_group(gl, (4 - r % 4) % 4, s, what);
+    if (gl.variant == 2) {
+        *what = "the streaming strip kernel does not cover this launch";
+        return cudaErrorInvalidValue;
+    }
     const v2::Layout2 L = st == Storage::F32   ? v2::make_layout2<float>(r, Dg, direct)
                           : st == Storage::F16 ? v2::make_layout2<__half>(r, Dg, direct)
                                                : v2::make_layout2<__nv_bfloat16>(r, Dg, direct);
-    const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
     CUtensorMap map;
-    if (!encode_frame_map(&map, st, gl.src, FW, FH, P, gl.src_pitch, L.BX, L.RH0)) {
+    if (gl.src_is_image) {
+        // the padding first pass: the copy engine reads the unpadded image at frame
+        // coordinates - r; the kernel replicates its border into the frame ring
+        if (!tstore || gl.src_pitch != W) {
+            *what = "a first pass from the unpadded image needs the tensor-store kernel";
+            return cudaErrorInvalidValue;
+        }
+        if (!encode_frame_map(&map, st, gl.src, W, H, P, W, L.BX, L.RH0)) {
+            *what = "cuTensorMapEncodeTiled failed (source image)";
+            return cudaErrorInvalidValue;
+        }
+    } else if (!encode_frame_map(&map, st, gl.src, FW, FH, P, gl.src_pitch, L.BX, L.RH0)) {
         *what = "cuTensorMapEncodeTiled failed (source frame)";
         return cudaErrorInvalidValue;
     }
@@ -204,9 +315,16 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     p.dst_is_output = last_out ? 1 : 0;
     p.dst_pitch = last_out ? W : gl.dst_pitch;
     p.dst_plane = last_out ? (long long)H * W : (long long)FH * gl.dst_pitch;
+    p.src_off = gl.src_is_image ? r : 0;
     // tile k spans frame columns [k*TW - shift, (k+1)*TW - shift)
     int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1 + shift) / v2::TW;
-    if (last_out && !gl.maps) {  // with maps, every frame pixel's selection is recorded
+    if (out_grid) {
+        // tile k spans frame columns [k*TW + r, (k+1)*TW + r) (rows likewise)
+        ty0 = gl.maps ? -1 : 0;
+        tx0 = gl.maps ? -1 : 0;
+        ty1 = gl.maps ? (FH - 1 - r) / v2::TH : (H - 1) / v2::TH;
+        tx1 = gl.maps ? (FW - 1 - r) / v2::TW : (W - 1) / v2::TW;
+    } else if (last_out && !gl.maps) {  // with maps, every frame pixel's selection is recorded
         ty0 = r / v2::TH;
         ty1 = (r + H - 1) / v2::TH;
         tx0 = (r + shift) / v2::TW;
@@ -214,12 +332,14 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     }
     p.ty_off = ty0;
     p.tx_off = tx0;
-    p.tx_shift = shift;
+    p.tx_shift = out_grid ? -r : shift;
+    p.ty_shift = out_grid ? -r : 0;
     p.tiles_x = tx1 - tx0 + 1;
     p.tiles_y = ty1 - ty0 + 1;
     CUtensorMap dmap;
-    if (tstore && !encode_store_map(&dmap, p.dst, FW, FH, P, p.dst_pitch)) {
-        *what = "cuTensorMapEncodeTiled failed (frame store map)";
+    if (tstore && !(last_out ? encode_store_map(&dmap, p.dst, W, H, P, W)
+                             : encode_store_map(&dmap, p.dst, FW, FH, P, p.dst_pitch))) {
+        *what = "cuTensorMapEncodeTiled failed (store map)";
         return cudaErrorInvalidValue;
     }
     const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
@@ -235,7 +355,7 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     if (occ < 1) occ = 1;
     const long long g = (long long)occ * gl.sms;
     const int grid = (int)(g < ntiles ? g : ntiles);
-    if (tstore) return launch_fwd2_tstore(r, false, map, dmap, p, grid, s);
+    if (tstore) return launch_fwd2_tstore(r, false, map, dmap, p, grid, s, gl.src_is_image != 0);
     switch (st) {
     case Storage::F16: return launch_fwd2_f16(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
     case Storage::BF16: return launch_fwd2_bf16(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
@@ -281,6 +401,11 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     int src_pitch = in_pitch;
     int cur = -1;  // index of the frame buffer holding the current state (-1: the caller's)
     int passes = 0;
+    // float32 tile passes at r % 4 == 0 (tensor stores, no maps): the first pass pads the
+    // image itself (the copy engine reads the unpadded rows; the image's pitch W must hold
+    // whole 16-byte groups), so no padding launch precedes it
+    const bool pad_fused = !in_is_frame && dtype == OSBF_F32 && tie == 0 && !maps && D == 1 && r % 4 == 0 &&
+                           W % 4 == 0 && ((uintptr_t)in & 15) == 0 && iters >= 2 && ctx->call_variant != 2;
     if (!in_is_frame) {
         if (dtype == OSBF_U8) {
             // exact integer first pass (plain loads with replicate padding) into a float frame
@@ -331,6 +456,10 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
             cur = 0;
             src = fb[0];
             src_pitch = FWp;
+        } else if (pad_fused) {
+            // the first pass reads the image itself and writes the padded frame's next state
+            src = in;
+            src_pitch = W;
         } else {
             void *f0 = frame(0);
             if (!f0) return OSBF_ENOMEM;
@@ -361,6 +490,8 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         gl.map_iter_stride = maps_iter_stride;
         gl.err = ctx->err_word;
         gl.sms = ctx->sms;
+        gl.variant = ctx->call_variant;
+        gl.src_is_image = pad_fused && passes == 0;
         int nxt = -1;
         if (last && !out_is_frame) {
             gl.dst = out;
@@ -484,6 +615,12 @@ osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int 
     if (o.tie != OSBF_TIE_PAPER && o.tie != OSBF_TIE_APPENDIX) return fail(ctx, OSBF_EINVAL, "unknown tie order");
     for (int v : o.reserved)
         if (v) return fail(ctx, OSBF_EINVAL, "reserved option fields must be zero");
+    if (o.variant < OSBF_VARIANT_AUTO || o.variant > OSBF_VARIANT_STRIP)
+        return fail(ctx, OSBF_EINVAL, "unknown forward variant %d", o.variant);
+    if (o.variant == OSBF_VARIANT_STRIP && (r > OSBF_STRIP_MAX_R || o.tie != OSBF_TIE_PAPER || dtype == OSBF_F16 ||
+                                            dtype == OSBF_BF16 || o.depth > 1))
+        return fail(ctx, OSBF_EUNSUPPORTED, "the strip kernel runs float32 single passes, paper tie order, r <= %d",
+                    OSBF_STRIP_MAX_R);
     if (r > OSBF_MAX_RADIUS) return fail(ctx, OSBF_EUNSUPPORTED, "r = %d exceeds OSBF_MAX_RADIUS = %d", r, OSBF_MAX_RADIUS);
     if (o.maps && (dtype == OSBF_F16 || dtype == OSBF_BF16) && o.tie != OSBF_TIE_PAPER)
         return fail(ctx, OSBF_EUNSUPPORTED, "16-bit storage keeps selection maps with the paper tie order only");
@@ -517,8 +654,11 @@ osbf_status osbf_filter_ex(osbf_ctx *ctx, const void *in, void *out, int N, int 
         }
         return OSBF_OK;
     }
-    return osbf_forward_run(ctx, in, 0, 0, out, 0, 0, (int)P, H, W, r, iters, dtype, o.depth, o.tie, o.maps, 0,
-                            map_stride, s);
+    ctx->call_variant = o.variant;
+    const osbf_status st = osbf_forward_run(ctx, in, 0, 0, out, 0, 0, (int)P, H, W, r, iters, dtype, o.depth, o.tie,
+                                            o.maps, 0, map_stride, s);
+    ctx->call_variant = 0;
+    return st;
 }
 
 osbf_status osbf_filter(osbf_ctx *ctx, const void *in, void *out, int N, int C, int H, int W, int r, int iters,

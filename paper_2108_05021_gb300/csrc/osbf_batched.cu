@@ -49,7 +49,17 @@ struct Job {
     float *frame[2];  // pass g writes frame[g & 1]
     int H, W, FH, FW, FWp, R, iters, tiles_x, ntiles, cnt_base;
     int shift;        // tile k starts at frame column k * TW - shift (TMA boxes start on 16 bytes)
+    // The last pass on the output-aligned grid (r % 4 == 0, W % 4 == 0, output on 16 bytes):
+    // tile k starts at frame row 32 (k / tiles_x_last) + r and column 128 (k % tiles_x_last)
+    // + r, as in a single filter call, whose last pass then shares these tiles' summation
+    // order; tiles_x_last x ceil(H / 32) = ntiles_last tiles cover the output.
+    int out_grid, tiles_x_last, ntiles_last;
 };
+
+// tiles of pass g of a job (the crop, pass `iters`, uses the frame grid)
+__device__ __forceinline__ int pass_tiles(const Job &jb, int g) {
+    return jb.out_grid && g == jb.iters - 1 ? jb.ntiles_last : jb.ntiles;
+}
 
 struct Params {
     unsigned long long wait_ns;  // bound of the dependency wait
@@ -114,8 +124,9 @@ __device__ void process(const Job &jb, int g, int tile, unsigned char *smem) {
     const v2::Layout2 L = v2::make_layout2<float>(R, 1, true);
     float *box = reinterpret_cast<float *>(smem + L.off_in);
     float *A = reinterpret_cast<float *>(smem + L.off_ab);
-    const int ty0 = (tile / jb.tiles_x) * v2::TH;
-    const int tx0 = (tile % jb.tiles_x) * v2::TW - jb.shift;
+    const bool og = jb.out_grid && g == jb.iters - 1;
+    const int ty0 = og ? (tile / jb.tiles_x_last) * v2::TH + R : (tile / jb.tiles_x) * v2::TH;
+    const int tx0 = og ? (tile % jb.tiles_x_last) * v2::TW + R : (tile % jb.tiles_x) * v2::TW - jb.shift;
     if (g == 0)
         load_padded_input(jb, L, box, ty0, tx0);
     else
@@ -176,7 +187,8 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
             // the job's previous pass must be complete (bounded wait)
             const volatile int *cnt = p.done + jb.cnt_base + g - 1;
             const unsigned long long t0 = now_ns();
-            while (*cnt < jb.ntiles) {
+            const int need = pass_tiles(jb, g - 1);
+            while (*cnt < need) {
                 if (now_ns() - t0 > p.wait_ns) {
                     atomicOr(p.err, 1u);
                     s_fail = 1;
@@ -313,6 +325,10 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
             b.shift = (4 - q.r % 4) % 4;
             b.tiles_x = (b.FW - 1 + b.shift) / v2::TW + 1;
             b.ntiles = b.tiles_x * ((b.FH + v2::TH - 1) / v2::TH);
+            // the single-call plan's condition for the output-aligned last pass
+            b.out_grid = q.r % 4 == 0 && q.W % 4 == 0 && ((uintptr_t)q.out & 15) == 0;
+            b.tiles_x_last = (q.W + v2::TW - 1) / v2::TW;
+            b.ntiles_last = b.tiles_x_last * ((q.H + v2::TH - 1) / v2::TH);
             b.cnt_base = cnt;
             cnt += b.iters + 1;  // the passes, then the crop
             max_iters = std::max(max_iters, b.iters);
@@ -323,7 +339,8 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
         for (int g = 0; g <= max_iters; ++g)
             for (size_t k = 0; k < hj.size(); ++k)
                 if (g <= hj[k].iters)
-                    for (int t = 0; t < hj[k].ntiles; ++t) items.push_back(make_int4((int)k, g, t, g == hj[k].iters));
+                    for (int t = 0; t < (hj[k].out_grid && g == hj[k].iters - 1 ? hj[k].ntiles_last : hj[k].ntiles); ++t)
+                        items.push_back(make_int4((int)k, g, t, g == hj[k].iters));
         // arena: jobs | items | next | counters | err | t_done | t_start | frames
         size_t off = 0;
         auto take = [&](size_t bytes) {

@@ -113,6 +113,7 @@ struct Fwd2Params {
     int tiles_x, tiles_y, ntiles;  // tile grid; ntiles = tiles_x * tiles_y * planes
     int ty_off, tx_off;
     int tx_shift;                  // tiles start at column k * TW - tx_shift (direct: float32 (4 - R % 4) % 4, 16-bit (8 - R % 8) % 8)
+    int src_off;                   // PADIN: the source is the unpadded image, at frame coordinates - src_off (= r)
     int ty_shift;                  // tiles start at row k * TH - ty_shift
     unsigned int *err;         // device error word (bit 0: a bounded wait gave up)
 };
@@ -156,6 +157,12 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t sr
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
                  "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+// 32-byte store of eight floats (the address is 32-byte aligned)
+__device__ __forceinline__ void st_global_v8(float *p, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -387,8 +394,13 @@ __device__ __forceinline__ void select2_exact(float2 d41, float2 d32, float2 d56
 // scattered 16-byte pieces per store instruction.
 // STREAM (the streaming strip kernel, osbf_strip.cuh): the rows of a, b and U live in
 // ring buffers; the caller passes this lane's row offsets (floats) sa, sb, su instead.
+// V8 (DIRECT float32, R % 4 == 0, the destination's columns at the segment start on 32
+// bytes): each lane writes its row's results eight at a time with one 32-byte store, an
+// 8-column group whenever its first column lies inside the destination row (groups are
+// aligned, so a destination whose width is a multiple of 8 -- or a frame, whose pitch
+// padding is never read -- takes whole groups); no staging buffer.
 template <int R, typename T, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false, bool STREAM = false>
+          bool XSTAGE = false, bool STREAM = false, bool V8 = false>
 __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in, int urow0,
                                         const float *__restrict__ A, int pa, float *__restrict__ Uout, int pu_out,
                                         T *__restrict__ gdst, long long gpitch, const Geom2 &g,
@@ -400,6 +412,8 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
     // lane per column: 32 consecutive floats per store instruction instead of a 16-byte
     // piece in each of 32 rows, at any grid shift
     static_assert(!XSTAGE || (DIRECT && sizeof(T) == 4 && !TSTORE), "result staging: direct float32");
+    static_assert(!V8 || (DIRECT && sizeof(T) == 4 && R % 4 == 0 && !TSTORE && !XSTAGE && !MAPS),
+                  "32-byte stores: direct float32, R % 4 == 0, no maps");
     // DIRECT maps: a warp's 32 x 32 selections are staged (byte b of a row holds output
     // b - MO; MO puts every full 4-group of the shifted grid on a word) and written out row
     // by row after the sweep, one byte per lane: 32 contiguous bytes per store instruction
@@ -457,6 +471,7 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
         float4 na = va, nb = vb, nu4 = vu;
         float o[4];
         uint2 held = make_uint2(0u, 0u);  // 16-bit DIRECT frames: the first half of a 16-byte store
+        float4 held8 = make_float4(0.f, 0.f, 0.f, 0.f);  // V8: the first half of a 32-byte store
         uint32_t mw = 0;  // DIRECT maps: selections of the current 4-column group
         // the whole segment is unrolled: ring slots, loads, warm-up and stores are static
 #pragma unroll
@@ -585,6 +600,12 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
                             }
                         } else if (XSTAGE) {
                             *reinterpret_cast<float4 *>(xst + lane * kOutPitch + oo - 3 + MO) = v;
+                        } else if (V8) {
+                            if ((oo & 7) == 3) {
+                                held8 = v;
+                            } else if (row_store && (unsigned)(dx - 4) < (unsigned)g.lx) {
+                                st_global_v8(grow + (oo - 7), held8, v);
+                            }
                         } else if (row_store && (unsigned)dx < (unsigned)g.lx) {
                             cvt_store4<T>(grow + (oo - 3), v);
                         }
@@ -658,11 +679,16 @@ __device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &
 // DIRECT: one pass per launch whose results (and selections, with MAPS) go from
 // registers straight into the destination (D == 1, halo EX == R); otherwise every pass
 // lands in shared memory and the tile interior is copied out at the end.
+// PADIN (first pass): the source tensor map is the unpadded image; the copy engine fills
+// zeros beyond it, and tiles touching its border then set every frame cell outside the
+// image to its nearest image cell (the appendix's replicate pad), which always lies in
+// the same box -- no separate padding pass.
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false>
+          bool XSTAGE = false, bool PADIN = false>
 __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !XSTAGE ? 4 : 3) : 2)
     osbf_fwd2(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dmap, const Fwd2Params p) {
     static_assert(!TSTORE || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0), "tensor stores: float32, R % 4 == 0");
+    static_assert(!PADIN || TSTORE, "the padding first pass: the tensor-store kernel");
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
     const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
@@ -689,14 +715,16 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
     auto issue = [&](int tile) {
         int plane, ty0, tx0;
         tile_origin(p, tile, plane, ty0, tx0);
-        tma_load_3d(smem_u32(bin), &src, tx0 - L.EX, ty0 - L.EY, plane, bar, (uint32_t)L.in_bytes);
+        const int so = PADIN ? p.src_off : 0;
+        tma_load_3d(smem_u32(bin), &src, tx0 - L.EX - so, ty0 - L.EY - so, plane, bar, (uint32_t)L.in_bytes);
     };
     // L2 prefetch of a tile's box: issued one tile ahead of its shared-memory load, so
     // that load is served from L2 instead of DRAM
     auto warm = [&](int tile) {
         int plane, ty0, tx0;
         tile_origin(p, tile, plane, ty0, tx0);
-        tma_prefetch_l2_3d(&src, tx0 - L.EX, ty0 - L.EY, plane);
+        const int so = PADIN ? p.src_off : 0;
+        tma_prefetch_l2_3d(&src, tx0 - L.EX - so, ty0 - L.EY - so, plane);
     };
     auto prefetch = [&](int tile) {
         const int next = tile + gridDim.x;
@@ -729,6 +757,34 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
             return;
         }
         phase ^= 1;
+        if (PADIN) {
+            // frame coordinates of the box origin; the image occupies [R, R+H) x [R, R+W)
+            const int by0 = ty0 - L.EY, bx0 = tx0 - L.EX;
+            if (by0 < R || by0 + L.RH0 > R + p.H || bx0 < R || bx0 + L.BX > R + p.W) {
+                float *ub = reinterpret_cast<float *>(bin);
+                // box rows and columns of the image and of the frame
+                const int iy0 = max(R - by0, 0), iy1 = min(R + p.H - by0, L.RH0);
+                const int ix0 = max(R - bx0, 0), ix1 = min(R + p.W - bx0, L.BX);
+                const int fy0 = max(-by0, 0), fy1 = min(p.FH - by0, L.RH0);
+                const int fx0 = max(-bx0, 0), fx1 = min(p.FW - bx0, L.BX);
+                // 1. image rows: the left and right frame-ring columns copy the image's edge column
+                const int nl = ix0 - fx0, nr = fx1 - ix1, ncol = nl + nr;
+                for (int i = threadIdx.x; i < (iy1 - iy0) * ncol; i += NT) {
+                    const int y = iy0 + i / ncol, k = i % ncol;
+                    const int x = k < nl ? fx0 + k : ix1 + (k - nl);
+                    ub[y * L.BX + x] = ub[y * L.BX + (k < nl ? ix0 : ix1 - 1)];
+                }
+                __syncthreads();
+                // 2. frame-ring rows above and below the image copy its edge row (now complete)
+                const int nt = iy0 - fy0, nb = fy1 - iy1, nrow = nt + nb, w = fx1 - fx0;
+                for (int i = threadIdx.x; i < nrow * w; i += NT) {
+                    const int k = i / w, x = fx0 + i % w;
+                    const int y = k < nt ? fy0 + k : iy1 + (k - nt);
+                    ub[y * L.BX + x] = ub[(k < nt ? iy0 : iy1 - 1) * L.BX + x];
+                }
+                __syncthreads();
+            }
+        }
 
         bool prefetched = false;
         if (sizeof(T) != 4) {  // widen the 16-bit box into the float buffer, then the box is free
@@ -832,11 +888,11 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
 
 // dmap: the destination's tensor map (read only by TSTORE kernels; any map otherwise)
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false>
+          bool XSTAGE = false, bool PADIN = false>
 cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream,
                         const CUtensorMap *dmap = nullptr) {
     const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE>;
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, PADIN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, L.bytes, stream>>>(src, dmap ? *dmap : src, p);

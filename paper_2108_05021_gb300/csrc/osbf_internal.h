@@ -44,8 +44,9 @@ cudaError_t launch_fwd2_fast(int R, bool maps, const CUtensorMap &src, const v2:
 int occupancy_fwd2_fast(int R, bool maps);
 
 // single-pass float32 launches with per-warp tensor stores (R % 4 == 0, paper tie order, no maps)
+// padin: the first pass straight from the unpadded image (replicate pad in the kernel)
 cudaError_t launch_fwd2_tstore(int R, bool fast, const CUtensorMap &src, const CUtensorMap &dmap,
-                               const v2::Fwd2Params &p, int grid, cudaStream_t s);
+                               const v2::Fwd2Params &p, int grid, cudaStream_t s, bool padin = false);
 int occupancy_fwd2_tstore(int R, bool fast);
 
 // A float32 destination for tensor stores: P planes of H rows x W elements (row pitch
@@ -73,8 +74,23 @@ struct GroupLaunch {
     long long map_iter_stride = 0;
     unsigned int *err = nullptr;  // device error word
     int sms = 0;
+    int variant = 0;  // forward kernel: 0 = library choice, 1 = tile kernel, 2 = streaming strip kernel
+    int src_is_image = 0;  // src is the caller's unpadded image (row pitch W): the first pass pads it itself
 };
 cudaError_t launch_group(const GroupLaunch &g, cudaStream_t s, const char **what);
+
+// streaming strip forward (osbf_strip.cuh, fwd2_strip.cu): float32, one pass per launch,
+// paper tie order, radii 1..OSBF_STRIP_MAX_R
+#define OSBF_STRIP_MAX_R 8
+namespace strip {
+struct StripParams;
+}
+// v8: results leave from registers by 32-byte stores (r % 4 == 0, no maps, the destination's
+// strip columns on 32 bytes); otherwise they are staged per warp and written row by row
+cudaError_t launch_fwd_strip(int R, bool maps, bool v8, const CUtensorMap &src, const strip::StripParams &sp,
+                             int grid, cudaStream_t s);
+int occupancy_fwd_strip(int R, bool maps, bool v8);
+int strip_box_width(int R);
 
 // the final crop of a float32 frame into H x W planes (osbf_misc.cu)
 cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W, int R, int FWp, cudaStream_t s);

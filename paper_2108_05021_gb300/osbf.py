@@ -25,6 +25,7 @@ _STATUS = {0: "OSBF_OK", 1: "OSBF_EINVAL", 2: "OSBF_ENOMEM", 3: "OSBF_ECUDA", 4:
            5: "OSBF_ETIMEOUT"}
 _DTYPE = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2, torch.uint8: 3}
 _TIE = {"paper": 0, "appendix": 1}
+_VARIANT = {"auto": 0, "tile": 1, "strip": 2}
 
 
 class OSBFError(RuntimeError):
@@ -36,7 +37,7 @@ class OSBFError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("tie", ctypes.c_int), ("maps", ctypes.c_void_p),
-                ("reserved", ctypes.c_int * 4)]
+                ("variant", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class _Job(ctypes.Structure):
@@ -181,8 +182,10 @@ def maps_frames(maps, W: int, r: int):
 
 
 def filter(x: torch.Tensor, r: int, iters: int, *, depth: int = 0, tie: str = "paper",
-           maps: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Forward One-Sided Box Filter (osbf_filter_ex).  uint8 input gives float32 output."""
+           maps: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+           variant: str = "auto") -> torch.Tensor:
+    """Forward One-Sided Box Filter (osbf_filter_ex).  uint8 input gives float32 output.
+    variant: the float32 single-pass kernel ("auto", "tile" or "strip")."""
     _require_cuda(x)
     N, C, H, W = _nchw(x)
     if x.dtype not in _DTYPE:
@@ -193,7 +196,7 @@ def filter(x: torch.Tensor, r: int, iters: int, *, depth: int = 0, tie: str = "p
     _require_cuda(out)
     if out.dtype != odt or out.shape != x.shape:
         raise ValueError("out has the wrong dtype or shape")
-    opts = _Options(depth, _TIE[tie], None, (ctypes.c_int * 4)())
+    opts = _Options(depth, _TIE[tie], None, _VARIANT[variant], (ctypes.c_int * 3)())
     if maps is not None:
         _require_cuda(maps)
         if maps.dtype != torch.uint8 or tuple(maps.shape) != maps_shape(x, r, iters):

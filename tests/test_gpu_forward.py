@@ -24,10 +24,10 @@ F32_TOL = 1e-5
 TIE_THRESH = 1e-6
 
 
-def gpu_filter(x_np, r, iters, depth=0, tie="paper", want_maps=True, dtype=torch.float32):
+def gpu_filter(x_np, r, iters, depth=0, tie="paper", want_maps=True, dtype=torch.float32, variant="auto"):
     x = torch.from_numpy(np.ascontiguousarray(x_np)).to(DEV).to(dtype)
     maps = torch.zeros(osbf.maps_shape(x, r, iters), dtype=torch.uint8, device=DEV) if want_maps else None
-    out = osbf.filter(x, r, iters, depth=depth, tie=tie, maps=maps)
+    out = osbf.filter(x, r, iters, depth=depth, tie=tie, maps=maps, variant=variant)
     torch.cuda.synchronize()
     return out.float().cpu().numpy(), (osbf.maps_frames(maps, x.shape[-1], r).cpu().numpy() if want_maps else None)
 
@@ -39,8 +39,8 @@ def gpu_filter(x_np, r, iters, depth=0, tie="paper", want_maps=True, dtype=torch
 MAX_HINTED_FRAC = 5e-3
 
 
-def check_f32(x_np, r, iters, depth=0, tie="paper", max_hinted_frac=MAX_HINTED_FRAC):
-    out, maps = gpu_filter(x_np, r, iters, depth=depth, tie=tie)
+def check_f32(x_np, r, iters, depth=0, tie="paper", max_hinted_frac=MAX_HINTED_FRAC, variant="auto"):
+    out, maps = gpu_filter(x_np, r, iters, depth=depth, tie=tie, variant=variant)
     ref = oracle.filter(x_np.astype(np.float64), r, iters, tie=tie, hint=maps, hint_thresh=TIE_THRESH,
                         want_gaps=True)
     err = np.abs(out.astype(np.float64) - ref["out"])
@@ -79,16 +79,21 @@ def test_literal_rule_one_pass():
         print(f"r={r}: near-tie pixels {(gap < TIE_THRESH).sum()}, max|d| elsewhere {err[gap >= TIE_THRESH].max():.3g}")
 
 
-@pytest.mark.parametrize("r", [1, 2, 3, 5, 8, 11, 16])
+# the two float32 single-pass kernels: "strip" covers r <= 8, "tile" every radius
+VARIANTS = [("tile", r) for r in (1, 2, 3, 5, 8, 11, 16)] + [("strip", r) for r in (1, 2, 3, 5, 6, 7, 8)]
+
+
+@pytest.mark.parametrize("variant,r", VARIANTS)
 @pytest.mark.parametrize("shape", [(1, 2, 70, 301), (2, 1, 131, 64)])
-def test_radii_ragged_tiles(shape, r):
+def test_radii_ragged_tiles(shape, variant, r):
     x = synth.piecewise_stack(*shape, seed=r, sigma=0.05)
-    check_f32(x, r, 3)
+    check_f32(x, r, 3, variant=variant)
 
 
-@pytest.mark.parametrize("r", [4, 8, 12, 16])
+@pytest.mark.parametrize("variant,r", [("tile", 4), ("tile", 8), ("tile", 12), ("tile", 16), ("strip", 4),
+                                       ("strip", 8)])
 @pytest.mark.parametrize("W", [256, 258])
-def test_no_maps_kernels_match_oracle(r, W):
+def test_no_maps_kernels_match_oracle(variant, r, W):
     """The kernels a plain call runs (no maps): frame-to-frame passes at r % 4 == 0 leave
     through per-warp tensor stores; the last pass writes the cropped output straight from
     the kernel when W % 4 == 0 (staged rows) and through the shared-memory kernel otherwise.
@@ -96,10 +101,25 @@ def test_no_maps_kernels_match_oracle(r, W):
     selections are the no-maps run's), and the oracle, hinted with those maps, agrees
     within 1e-5 on every pixel."""
     x = synth.piecewise_stack(1, 2, 97, W, seed=60 + r, sigma=0.05)
-    plain, _ = gpu_filter(x, r, 4, want_maps=False)
-    out, maps, ref = check_f32(x, r, 4)
+    plain, _ = gpu_filter(x, r, 4, want_maps=False, variant=variant)
+    out, maps, ref = check_f32(x, r, 4, variant=variant)
     np.testing.assert_array_equal(plain, out)
     assert np.abs(plain.astype(np.float64) - ref["out"]).max() <= F32_TOL
+
+
+@pytest.mark.parametrize("r", [4, 8, 16])
+@pytest.mark.parametrize("shape", [(1, 1, 1, 4), (1, 1, 3, 8), (1, 2, 29, 4), (2, 1, 70, 132), (1, 1, 40, 300)])
+def test_padding_first_pass(shape, r):
+    """Float32 at r % 4 == 0 with W % 4 == 0: the first pass reads the unpadded image and
+    replicates its border into the frame ring itself (no padding launch).  Images smaller
+    than r, one row high and spanning several tiles: the plain call equals the map-writing
+    call, which pads with a separate launch, bit for bit, and the oracle within 1e-5."""
+    x = synth.piecewise_stack(*shape, seed=70 + r, sigma=0.05)
+    plain, _ = gpu_filter(x, r, 3, want_maps=False)
+    launches = osbf.last_launch_count(0)
+    out, maps, ref = check_f32(x, r, 3, max_hinted_frac=0.05)
+    np.testing.assert_array_equal(plain, out)
+    assert launches == 3  # three passes, no padding launch
 
 
 def test_bench_shape_sampled():
