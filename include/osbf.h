@@ -242,14 +242,28 @@ typedef struct {
  * one persistent launch (a device-side queue of (job, fused pass group, tile) items
  * in group-round order; an item starts once its job's previous group has finished),
  * replayed from a CUDA graph that the context caches per job signature (sizes,
- * radii, pass counts and pointers).  Equivalent to one osbf_filter() per job
- * (float32, paper tie order) up to float32 summation order.  Jobs with r = 0 or
- * iters = 0 are copies; jobs with r > 8 run as separate filter calls.  Synchronous.
+ * radii, pass counts and pointers, and the tuned policy, see osbf_autotune_batched()).
+ * Equivalent to one osbf_filter() per job (float32, paper tie order), bit for bit with the
+ * untuned single-call plan.  Jobs with r = 0 or iters = 0 are copies; jobs with r > 8, and
+ * jobs whose tuned single-call choice (osbf_autotune) is another kernel or depth, run as
+ * separate filter calls.  Synchronous.
  * Returns OSBF_EINVAL for a bad job (null pointer, non-positive size, in == out),
  * OSBF_ETIMEOUT if a bounded device-side wait gave up (outputs then undefined; the
  * context stays usable).
  */
 osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream);
+
+/* Tune the batched launch of this job list (synchronous; runs the batch several times): time
+ * each layout policy -- the job order within every pass round (as given, or by decreasing
+ * H x W x passes) and the resident CTAs per SM (as many as fit, or one fewer) -- each from
+ * its own cached graph, and record the fastest for the job signature; later
+ * osbf_filter_batched() calls with the same jobs replay that policy's graph.  The policy
+ * changes the schedule, never the results. */
+osbf_status osbf_autotune_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream);
+
+/* The tuned policy of this job list: *order (0 as given, 1 by decreasing work) and
+ * *ctas_per_sm; returns 1 if one is recorded, else 0 (the defaults 0, as many as fit). */
+int osbf_batched_policy(osbf_ctx *ctx, const osbf_job *jobs, int njobs, int *order, int *ctas_per_sm);
 
 /* Per-image latency of the last osbf_filter_batched() call: for each job of its
  * persistent launch (jobs with 1 <= r <= 8 and iters >= 1, in job order), the
@@ -257,10 +271,24 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
  * the number of values written to ns (at most cap).  Synchronous. */
 int osbf_batched_latencies(osbf_ctx *ctx, unsigned long long *ns, int cap);
 
-/* Tune the fused depth for (dtype, r) on an H x W x planes problem by timing the
- * candidates on the device (synchronous); later calls with depth 0 -- the plain,
- * checkpointed and batched forms -- use it. */
+/* Tune the forward for (dtype, r) on a planes x H x W problem with `iters` passes: time, on
+ * the device (synchronous), every candidate -- the tile kernel at each fused depth that fits
+ * shared memory and, for float32 (and 8-bit input's float32 passes) at r <= 8, the streaming
+ * strip kernel -- on a synthetic non-constant image generated in device memory, and record
+ * the fastest {depth, variant} for (dtype, r, the problem's size class: pixels in factors of
+ * 4 above 2^20).  Later calls with depth 0 and variant OSBF_VARIANT_AUTO -- plain, map-writing
+ * and checkpointed forwards -- use it; the choice is a kernel and a depth, never a change
+ * of the filter.  Allocates two scratch images for the duration of the call. */
 osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int iters);
+
+/* Record a tuned choice without timing (for instance one found on an earlier run):
+ * depth 1..OSBF_MAX_DEPTH, variant OSBF_VARIANT_TILE or OSBF_VARIANT_STRIP (depth 1, float32
+ * or 8-bit input, r <= 8; else OSBF_EUNSUPPORTED). */
+osbf_status osbf_set_tuned(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int depth, int variant);
+
+/* The tuned choice recorded for (dtype, r, the size class of planes x H x W): *depth and
+ * *variant (osbf_variant); both 0 when nothing was tuned for it. */
+osbf_status osbf_tuned(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int *depth, int *variant);
 
 /* Synchronise the context's device and report whether any kernel of this context
  * gave up a bounded device-side wait since the last check (OSBF_ETIMEOUT; the

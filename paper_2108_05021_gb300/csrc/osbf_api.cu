@@ -29,7 +29,8 @@ struct osbf_ctx {
     void *ws[4] = {nullptr, nullptr, nullptr, nullptr};  // backward / checkpoint workspaces
     size_t ws_bytes[4] = {0, 0, 0, 0};
     int last_launches = 0;
-    std::map<std::tuple<int, int, int>, int> tuned;  // (dtype, r, size class) -> depth
+    // (dtype, r, size class) -> the tuned forward: {fused depth, osbf_variant}
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     void *batch_state = nullptr;                     // owned by the batched launcher
     unsigned int *err_word = nullptr;                // device: bit 0 = a bounded device wait gave up
     unsigned long long wait_ns = 0;                  // bound of the batched dependency wait (0 = default)
@@ -379,9 +380,13 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     const int MP = maps_pitch(FW);
 
     int D = depth > 0 ? depth : 0;
+    int variant = ctx->call_variant;
     if (D == 0) {
+        // the tuned choice (osbf_autotune) applies when the caller fixed neither the depth
+        // nor the kernel
         auto it = ctx->tuned.find(std::make_tuple((int)dtype, r, size_class((long long)P * H * W)));
-        D = it != ctx->tuned.end() ? it->second : default_depth(r, dtype);
+        D = it != ctx->tuned.end() ? it->second.first : default_depth(r, dtype);
+        if (variant == 0 && it != ctx->tuned.end()) variant = it->second.second;
     }
     if (D > OSBF_MAX_DEPTH) D = OSBF_MAX_DEPTH;
     D = fit_depth(ctx, st, r, D);
@@ -405,7 +410,7 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     // image itself (the copy engine reads the unpadded rows; the image's pitch W must hold
     // whole 16-byte groups), so no padding launch precedes it
     const bool pad_fused = !in_is_frame && dtype == OSBF_F32 && tie == 0 && !maps && D == 1 && r % 4 == 0 &&
-                           W % 4 == 0 && ((uintptr_t)in & 15) == 0 && iters >= 2 && ctx->call_variant != 2;
+                           W % 4 == 0 && ((uintptr_t)in & 15) == 0 && iters >= 2 && variant != OSBF_VARIANT_STRIP;
     if (!in_is_frame) {
         if (dtype == OSBF_U8) {
             // exact integer first pass (plain loads with replicate padding) into a float frame
@@ -490,7 +495,7 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         gl.map_iter_stride = maps_iter_stride;
         gl.err = ctx->err_word;
         gl.sms = ctx->sms;
-        gl.variant = ctx->call_variant;
+        gl.variant = variant;
         gl.src_is_image = pad_fused && passes == 0;
         int nxt = -1;
         if (last && !out_is_frame) {
@@ -750,20 +755,31 @@ osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, in
         if (din) cudaFree(din);
         return fail(ctx, OSBF_ENOMEM, "tuning buffers");
     }
-    cudaMemset(din, 0, in_bytes);
     cudaStream_t s = nullptr;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const Storage st = storage_of(dtype);
-    int best_d = 1;
-    float best_ms = 1e30f;
     osbf_status status = OSBF_OK;
-    for (int D = 1; D <= OSBF_MAX_DEPTH; ++D) {
-        if (D > iters || fwd_smem(st, r, D) > ctx->smem_optin) break;
+    if (launch_tuning_image(st, din, planes, H, W, s) != cudaSuccess)
+        status = fail(ctx, OSBF_ECUDA, "tuning image fill failed");
+    // candidates: the tile kernel at every fused depth that fits (a larger requested depth
+    // is clamped to the largest that fits, so stop at the first clamped one), and the
+    // streaming strip kernel for float32 single passes
+    std::vector<std::pair<int, int>> cand;  // {depth, variant}
+    const Storage fst = dtype == OSBF_U8 ? Storage::F32 : st;
+    for (int D = 1; D <= OSBF_MAX_DEPTH && D <= iters; ++D) {
+        if (fit_depth(ctx, fst, r, D) != D) break;
+        cand.push_back({D, OSBF_VARIANT_TILE});
+    }
+    if ((dtype == OSBF_F32 || dtype == OSBF_U8) && r <= OSBF_STRIP_MAX_R) cand.push_back({1, OSBF_VARIANT_STRIP});
+    std::pair<int, int> best = {1, OSBF_VARIANT_TILE};
+    float best_ms = 1e30f;
+    for (size_t c = 0; c < cand.size() && status == OSBF_OK; ++c) {
         osbf_options o;
         std::memset(&o, 0, sizeof o);
-        o.depth = D;
+        o.depth = cand[c].first;
+        o.variant = cand[c].second;
         status = osbf_filter_ex(ctx, din, dout, planes, 1, H, W, r, iters, dtype, &o, s);  // warm-up
         if (status) break;
         cudaEventRecord(e0, s);
@@ -777,7 +793,7 @@ osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, in
         if (status) break;
         if (ms < best_ms) {
             best_ms = ms;
-            best_d = D;
+            best = cand[c];
         }
     }
     cudaEventDestroy(e0);
@@ -785,7 +801,34 @@ osbf_status osbf_autotune(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, in
     cudaFree(din);
     cudaFree(dout);
     if (status) return status;
-    ctx->tuned[std::make_tuple((int)dtype, r, size_class((long long)planes * H * W))] = best_d;
+    ctx->tuned[std::make_tuple((int)dtype, r, size_class((long long)planes * H * W))] = best;
+    return OSBF_OK;
+}
+
+osbf_status osbf_set_tuned(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int depth, int variant) {
+    if (!ctx) return OSBF_EINVAL;
+    ctx->err.clear();
+    if (planes <= 0 || H <= 0 || W <= 0 || r < 1 || r > OSBF_MAX_RADIUS || dtype < OSBF_F32 || dtype > OSBF_U8)
+        return fail(ctx, OSBF_EINVAL, "bad tuning key");
+    if (depth < 1 || depth > OSBF_MAX_DEPTH || variant < OSBF_VARIANT_TILE || variant > OSBF_VARIANT_STRIP)
+        return fail(ctx, OSBF_EINVAL, "bad tuned choice");
+    if (variant == OSBF_VARIANT_STRIP &&
+        (depth != 1 || r > OSBF_STRIP_MAX_R || dtype == OSBF_F16 || dtype == OSBF_BF16))
+        return fail(ctx, OSBF_EUNSUPPORTED, "the strip kernel runs float32 single passes at r <= %d", OSBF_STRIP_MAX_R);
+    ctx->tuned[std::make_tuple((int)dtype, r, size_class((long long)planes * H * W))] = {depth, variant};
+    return OSBF_OK;
+}
+
+osbf_status osbf_tuned(osbf_ctx *ctx, osbf_dtype dtype, int planes, int H, int W, int r, int *depth, int *variant) {
+    if (!ctx || !depth || !variant) return OSBF_EINVAL;
+    auto it = ctx->tuned.find(std::make_tuple((int)dtype, r, size_class((long long)planes * H * W)));
+    if (it == ctx->tuned.end()) {
+        *depth = 0;
+        *variant = OSBF_VARIANT_AUTO;
+        return OSBF_OK;
+    }
+    *depth = it->second.first;
+    *variant = it->second.second;
     return OSBF_OK;
 }
 
@@ -937,7 +980,12 @@ unsigned int *osbf_ctx_err_word(osbf_ctx *ctx) { return ctx->err_word; }
 unsigned long long osbf_ctx_wait_ns(const osbf_ctx *ctx) { return ctx->wait_ns; }
 int osbf_ctx_tuned_depth(osbf_ctx *ctx, osbf_dtype dt, int r, long long pixels) {
     auto it = ctx->tuned.find(std::make_tuple((int)dt, r, size_class(pixels)));
-    return it != ctx->tuned.end() ? it->second : default_depth(r, dt);
+    return it != ctx->tuned.end() ? it->second.first : default_depth(r, dt);
+}
+// a tuned float32 choice other than the tile kernel at depth 1 (the batched launch's own)
+bool osbf_ctx_tuned_elsewhere(osbf_ctx *ctx, int r, long long pixels) {
+    auto it = ctx->tuned.find(std::make_tuple((int)OSBF_F32, r, size_class(pixels)));
+    return it != ctx->tuned.end() && (it->second.first != 1 || it->second.second == OSBF_VARIANT_STRIP);
 }
 void *osbf_ctx_workspace(osbf_ctx *ctx, int slot, size_t bytes, osbf_status *st) {
     *st = ensure(ctx, &ctx->ws[slot], &ctx->ws_bytes[slot], bytes);

@@ -240,8 +240,17 @@ struct Planned {
     int njobs = 0;
 };
 
+// How a batch is laid out and launched: the job order within each pass round (0: as given,
+// 1: by decreasing work, H x W x passes, so the longest chains start first) and the
+// resident CTAs per SM.  osbf_autotune_batched() times the candidates on the batch itself.
+struct Policy {
+    int order = 0;
+    int ctas_per_sm = 0;  // 0: as many as fit
+};
+
 struct BatchState {
-    std::map<std::vector<long long>, Planned> plans;  // job signature -> graph and arena
+    std::map<std::vector<long long>, Planned> plans;  // job signature + policy -> graph and arena
+    std::map<std::vector<long long>, Policy> tuned;   // job signature -> tuned policy
     const Planned *last = nullptr;                    // for osbf_batched_latencies()
 };
 
@@ -265,9 +274,33 @@ void osbf_batched_free(osbf_ctx *ctx) {
     *slot = nullptr;
 }
 
-extern "C" {
+bool osbf_ctx_tuned_elsewhere(osbf_ctx *ctx, int r, long long pixels);
 
-osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream) {
+namespace {
+
+// Jobs the persistent launch takes: 1 <= r <= 8, iters >= 1, and no tuned single-call
+// choice of another kernel or depth (those run as plain filter calls).
+bool persistent_job(osbf_ctx *ctx, const osbf_job &q) {
+    return q.r >= 1 && q.iters >= 1 && q.r <= batched::kMaxR &&
+           !osbf_ctx_tuned_elsewhere(ctx, q.r, (long long)q.H * q.W);
+}
+
+// The job signature: the batch size, the wait bound and every persistent job's pointers,
+// sizes, radius and pass count (the key of the cached graphs and of the tuned policies).
+std::vector<long long> job_signature(osbf_ctx *ctx, const osbf_job *jobs, int njobs) {
+    std::vector<long long> sig;
+    sig.push_back(njobs);
+    sig.push_back((long long)osbf_ctx_wait_ns(ctx));
+    for (int j = 0; j < njobs; ++j) {
+        const osbf_job &q = jobs[j];
+        if (persistent_job(ctx, q))
+            sig.insert(sig.end(), {(long long)(uintptr_t)q.in, (long long)(uintptr_t)q.out, q.H, q.W, q.r, q.iters});
+    }
+    return sig;
+}
+
+// The batched call with a given policy (force), or with the tuned one (force == nullptr).
+osbf_status batched_run(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream, const Policy *force) {
     if (!ctx) return OSBF_EINVAL;
     osbf_ctx_reset_launches(ctx);
     if (njobs < 0 || (njobs > 0 && !jobs)) return osbf_ctx_fail(ctx, OSBF_EINVAL, "bad job list");
@@ -283,26 +316,34 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
 
     // the persistent launch takes jobs with 1 <= r <= 8 and iters >= 1; the rest run alone
     std::vector<int> pj;
-    std::vector<long long> sig;
-    sig.push_back(njobs);
-    sig.push_back((long long)osbf_ctx_wait_ns(ctx));
+    std::vector<long long> sig = job_signature(ctx, jobs, njobs);
     for (int j = 0; j < njobs; ++j) {
         const osbf_job &q = jobs[j];
         if (q.r == 0 || q.iters == 0) {
             if (cudaMemcpyAsync(q.out, q.in, sizeof(float) * (size_t)q.H * q.W, cudaMemcpyDeviceToDevice, s) !=
                 cudaSuccess)
                 return osbf_ctx_fail(ctx, OSBF_ECUDA, "copy failed");
-        } else if (q.r > batched::kMaxR) {
+        } else if (!persistent_job(ctx, q)) {
+            // radii beyond the persistent kernel's, and jobs whose tuned forward is another
+            // kernel or depth: a plain filter call each (which applies the tuned choice)
             osbf_status e = osbf_forward_run(ctx, q.in, 0, 0, q.out, 0, 0, 1, q.H, q.W, q.r, q.iters, OSBF_F32, 0, 0,
                                              nullptr, 0, 0, s);
             if (e) return e;
         } else {
             pj.push_back(j);
-            sig.insert(sig.end(), {(long long)(uintptr_t)q.in, (long long)(uintptr_t)q.out, q.H, q.W, q.r, q.iters});
         }
     }
     if (pj.empty()) return OSBF_OK;
 
+    Policy pol;
+    if (force) {
+        pol = *force;
+    } else {
+        auto tit = bs->tuned.find(sig);
+        if (tit != bs->tuned.end()) pol = tit->second;
+    }
+    sig.push_back(pol.order);
+    sig.push_back(pol.ctas_per_sm);
     auto git = bs->plans.find(sig);
     if (git == bs->plans.end()) {
         // ---- plan: jobs, items in round order, counters, arena ----
@@ -335,9 +376,15 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
             frame_floats += 2 * (size_t)b.FH * b.FWp;
             smem = std::max(smem, (size_t)v2::make_layout2<float>(q.r, 1, true).bytes);
         }
+        std::vector<size_t> korder(hj.size());
+        for (size_t k = 0; k < hj.size(); ++k) korder[k] = k;
+        if (pol.order == 1)
+            std::stable_sort(korder.begin(), korder.end(), [&](size_t a, size_t b) {
+                return (long long)hj[a].H * hj[a].W * hj[a].iters > (long long)hj[b].H * hj[b].W * hj[b].iters;
+            });
         std::vector<int4> items;
         for (int g = 0; g <= max_iters; ++g)
-            for (size_t k = 0; k < hj.size(); ++k)
+            for (size_t k : korder)
                 if (g <= hj[k].iters)
                     for (int t = 0; t < (hj[k].out_grid && g == hj[k].iters - 1 ? hj[k].ntiles_last : hj[k].ntiles); ++t)
                         items.push_back(make_int4((int)k, g, t, g == hj[k].iters));
@@ -393,6 +440,7 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched::osbf_batched_kernel, v2::NT, smem);
         if (occ < 1) occ = 1;
+        if (pol.ctas_per_sm > 0 && pol.ctas_per_sm < occ) occ = pol.ctas_per_sm;
         int grid = occ * osbf_ctx_sms(ctx);  // all CTAs resident: every wait is on a running CTA
         if (grid > (int)items.size()) grid = (int)items.size();
 
@@ -441,6 +489,85 @@ osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, 
         return osbf_ctx_fail(ctx, OSBF_ECUDA, "batched launch failed");
     if (w) return osbf_ctx_fail(ctx, OSBF_ETIMEOUT, "a batched item waited too long for its previous pass");
     return OSBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream) {
+    return batched_run(ctx, jobs, njobs, stream, nullptr);
+}
+
+osbf_status osbf_autotune_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream) {
+    if (!ctx) return OSBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int occ = 0;
+    {
+        size_t smem = 0;
+        for (int j = 0; j < njobs; ++j)
+            if (jobs && persistent_job(ctx, jobs[j]))
+                smem = std::max(smem, (size_t)v2::make_layout2<float>(jobs[j].r, 1, true).bytes);
+        if (smem == 0) return batched_run(ctx, jobs, njobs, stream, nullptr);  // nothing to tune
+        if (cudaFuncSetAttribute(batched::osbf_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched::osbf_batched_kernel, v2::NT, smem) !=
+                cudaSuccess)
+            return osbf_ctx_fail(ctx, OSBF_ECUDA, "occupancy query failed");
+        if (occ < 1) occ = 1;
+    }
+    std::vector<Policy> cand;
+    for (int order = 0; order < 2; ++order)
+        for (int c = occ; c >= 1 && c >= occ - 1; --c) {
+            Policy p;
+            p.order = order;
+            p.ctas_per_sm = c;
+            cand.push_back(p);
+        }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Policy best = cand[0];
+    float best_ms = 1e30f;
+    osbf_status st = OSBF_OK;
+    for (const Policy &p : cand) {
+        st = batched_run(ctx, jobs, njobs, stream, &p);  // builds and caches this policy's graph
+        if (st) break;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 3 && !st; ++k) st = batched_run(ctx, jobs, njobs, stream, &p);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    // record it under the job signature (the same key osbf_filter_batched() looks up)
+    BatchState *bs = state(ctx);
+    const std::vector<long long> sig = job_signature(ctx, jobs, njobs);
+    bs->tuned[sig] = best;
+    return OSBF_OK;
+}
+
+int osbf_batched_policy(osbf_ctx *ctx, const osbf_job *jobs, int njobs, int *order, int *ctas_per_sm) {
+    if (!ctx || !order || !ctas_per_sm) return 0;
+    BatchState *bs = state(ctx);
+    const std::vector<long long> sig = job_signature(ctx, jobs, njobs);
+    auto it = bs->tuned.find(sig);
+    if (it == bs->tuned.end()) {
+        *order = 0;
+        *ctas_per_sm = 0;
+        return 0;
+    }
+    *order = it->second.order;
+    *ctas_per_sm = it->second.ctas_per_sm;
+    return 1;
 }
 
 // Per-image latency of the last osbf_filter_batched() call on `ctx` (see osbf.h).

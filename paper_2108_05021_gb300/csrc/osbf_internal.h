@@ -98,5 +98,7 @@ cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W,
 // elementwise helpers (osbf_misc.cu)
 cudaError_t launch_u8_to_f32(const uint8_t *in, float *out, long long n, cudaStream_t s);
 cudaError_t launch_fill_u8(uint8_t *p, uint8_t v, long long n, cudaStream_t s);
+// a non-constant synthetic image (P planes of H x W) in the given storage type, for tuning
+cudaError_t launch_tuning_image(Storage st, void *p, int P, int H, int W, cudaStream_t s);
 
 }  // namespace osbf

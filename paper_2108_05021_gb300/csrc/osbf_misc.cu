@@ -13,6 +13,34 @@ __global__ void fill_u8_kernel(uint8_t *__restrict__ p, uint8_t v, long long n) 
         p[i] = v;
 }
 
+// A synthetic image for tuning: 64 x 64 blocks of hashed levels in [0, 1] plus hashed
+// noise of amplitude 0.05, clamped (values only need to be non-constant and image-like:
+// the filter's cost does not depend on them, but a constant image would let every
+// selection tie).  8-bit storage gets round(255 v).
+__device__ __forceinline__ float hash01(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return (x >> 8) * (1.0f / 16777216.0f);
+}
+
+template <typename T>
+__global__ void tuning_image_kernel(T *__restrict__ p, int H, int W, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long plane = i / ((long long)H * W);
+        const int rem = (int)(i - plane * H * (long long)W), y = rem / W, x = rem - y * W;
+        const unsigned cell = (unsigned)(plane * 7919 + (y >> 6) * 104729 + (x >> 6));
+        float v = hash01(cell * 2654435761u) + 0.1f * (hash01((unsigned)i * 2246822519u + 7u) - 0.5f);
+        v = fminf(fmaxf(v, 0.f), 1.f);
+        if constexpr (sizeof(T) == 1)
+            p[i] = (T)__float2int_rn(255.f * v);
+        else
+            p[i] = from_f<T>(v);
+    }
+}
+
 static int grid_for(long long n) {
     long long g = (n + 255) / 256;
     return (int)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
@@ -20,6 +48,19 @@ static int grid_for(long long n) {
 
 cudaError_t launch_u8_to_f32(const uint8_t *in, float *out, long long n, cudaStream_t s) {
     u8_to_f32_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tuning_image(Storage st, void *p, int P, int H, int W, cudaStream_t s) {
+    const long long n = (long long)P * H * W;
+    switch (st) {
+    case Storage::F32: tuning_image_kernel<float><<<grid_for(n), 256, 0, s>>>((float *)p, H, W, n); break;
+    case Storage::F16: tuning_image_kernel<__half><<<grid_for(n), 256, 0, s>>>((__half *)p, H, W, n); break;
+    case Storage::BF16:
+        tuning_image_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>((__nv_bfloat16 *)p, H, W, n);
+        break;
+    case Storage::U8: tuning_image_kernel<uint8_t><<<grid_for(n), 256, 0, s>>>((uint8_t *)p, H, W, n); break;
+    }
     return cudaGetLastError();
 }
 

@@ -89,6 +89,14 @@ def lib() -> ctypes.CDLL:
         L.osbf_filter_batched.restype = st
         L.osbf_autotune.argtypes = [vp, i, i, i, i, i, i]
         L.osbf_autotune.restype = st
+        L.osbf_tuned.argtypes = [vp, i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.osbf_tuned.restype = st
+        L.osbf_set_tuned.argtypes = [vp, i, i, i, i, i, i, i]
+        L.osbf_set_tuned.restype = st
+        L.osbf_autotune_batched.argtypes = [vp, ctypes.POINTER(_Job), i, vp]
+        L.osbf_autotune_batched.restype = st
+        L.osbf_batched_policy.argtypes = [vp, ctypes.POINTER(_Job), i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.osbf_batched_policy.restype = i
         L.osbf_frame_pitch.argtypes = [i, i]
         L.osbf_frame_pitch.restype = i
         L.osbf_maps_pitch.argtypes = [i, i]
@@ -365,12 +373,8 @@ def backward_checkpointed(grad_out: torch.Tensor, checkpoints: torch.Tensor, r: 
     return out
 
 
-def batched(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequence[int],
-            outputs: Optional[Sequence[torch.Tensor]] = None) -> list:
-    """osbf_filter_batched: many H x W float32 images of different sizes, radii and pass counts."""
+def _jobs(inputs, radii, iters, outputs):
     n = len(inputs)
-    if outputs is None:
-        outputs = [torch.empty_like(t) for t in inputs]
     jobs = (_Job * n)()
     dev = None
     for k, (t, o, r, it) in enumerate(zip(inputs, outputs, radii, iters)):
@@ -379,10 +383,42 @@ def batched(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequenc
             raise ValueError("batched jobs are H x W float32 images")
         dev = t.device.index if dev is None else dev
         jobs[k] = _Job(t.data_ptr(), o.data_ptr(), t.shape[0], t.shape[1], int(r), int(it))
-    dev = 0 if dev is None else dev
+    return jobs, n, 0 if dev is None else dev
+
+
+def batched(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequence[int],
+            outputs: Optional[Sequence[torch.Tensor]] = None) -> list:
+    """osbf_filter_batched: many H x W float32 images of different sizes, radii and pass counts."""
+    if outputs is None:
+        outputs = [torch.empty_like(t) for t in inputs]
+    jobs, n, dev = _jobs(inputs, radii, iters, outputs)
     ctx = context(dev)
     _check(lib().osbf_filter_batched(ctx, jobs, n, _stream(dev)), ctx)
     return list(outputs)
+
+
+def autotune_batched(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequence[int],
+                     outputs: Sequence[torch.Tensor]) -> None:
+    """osbf_autotune_batched: time the batch's layout policies, record the fastest for these jobs."""
+    jobs, n, dev = _jobs(inputs, radii, iters, outputs)
+    ctx = context(dev)
+    _check(lib().osbf_autotune_batched(ctx, jobs, n, _stream(dev)), ctx)
+
+
+def batched_policy(inputs: Sequence[torch.Tensor], radii: Sequence[int], iters: Sequence[int],
+                   outputs: Sequence[torch.Tensor]):
+    """The tuned policy of these jobs as (order, ctas_per_sm), or None if none is recorded."""
+    jobs, n, dev = _jobs(inputs, radii, iters, outputs)
+    o, c = ctypes.c_int(), ctypes.c_int()
+    found = lib().osbf_batched_policy(context(dev), jobs, n, ctypes.byref(o), ctypes.byref(c))
+    return (o.value, c.value) if found else None
+
+
+def set_tuned(dtype: torch.dtype, planes: int, H: int, W: int, r: int, depth: int, variant: str,
+              device: int = 0) -> None:
+    """osbf_set_tuned: record a forward choice (depth, "tile" or "strip") without timing."""
+    ctx = context(device)
+    _check(lib().osbf_set_tuned(ctx, _DTYPE[dtype], planes, H, W, r, depth, _VARIANT[variant]), ctx)
 
 
 def set_wait_timeout(ns: int, device: int = 0) -> None:
@@ -399,9 +435,19 @@ def batched_latencies(n: int, device: int = 0) -> list:
 
 
 def autotune(dtype: torch.dtype, planes: int, H: int, W: int, r: int, iters: int, device: int = 0) -> None:
+    """osbf_autotune: time the forward's candidates (tile kernel at each fused depth, strip
+    kernel) on a synthetic image and record the fastest for (dtype, r, size class)."""
     ctx = context(device)
     with torch.cuda.device(device):
         _check(lib().osbf_autotune(ctx, _DTYPE[dtype], planes, H, W, r, iters), ctx)
+
+
+def tuned(dtype: torch.dtype, planes: int, H: int, W: int, r: int, device: int = 0):
+    """The recorded tuned choice as (depth, variant name), or (0, "auto") if none."""
+    d, v = ctypes.c_int(), ctypes.c_int()
+    ctx = context(device)
+    _check(lib().osbf_tuned(ctx, _DTYPE[dtype], planes, H, W, r, ctypes.byref(d), ctypes.byref(v)), ctx)
+    return d.value, {0: "auto", 1: "tile", 2: "strip"}[v.value]
 
 
 class OSBFFunction(torch.autograd.Function):
