@@ -50,9 +50,10 @@ N_, C_, H_, W_, R_, ITERS_ = 1, 3, 4096, 4096, 8, 30
 WORKLOAD = "osbf forward, 1x3x4096x4096 float32, r=8, 30 passes, piecewise-constant+noise (sigma 0.05)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) of one forward launch of the headline workload, from one ncu
-# capture of that launch (to be reset to None whenever the kernel changes)
-TRAFFIC_PER_LAUNCH = 364.5e6
+# DRAM bytes (read + write) of one frame-to-frame launch of the headline workload's tile
+# kernel (tensor stores), from one ncu capture of that launch: 204.4 MB read + 160.8 MB
+# written (reset to None whenever that kernel changes)
+TRAFFIC_PER_LAUNCH = 365.2e6
 
 
 def hbm_peak():
@@ -140,7 +141,9 @@ class ClockSampler:
 
 def cpu_baseline_sample(x_plane: np.ndarray, seconds_hint: float = 10.0):
     """The oracle (as it stands) on the host cores: 1024 x 1024 crop, r = 8, enough passes
-    for about `seconds_hint` seconds of work.  Returns (Mpixel*iter/s, cores, description)."""
+    for about `seconds_hint` seconds of work.  Returns (Mpixel*iter/s, cores, description,
+    near ties): the literal FP32 rule's count of output pixels whose best two |d_i| differ
+    by less than 1e-6 in the sample's last pass (taken from the same run's gaps)."""
     import oracle
 
     crop = np.ascontiguousarray(x_plane[:1024, :1024], dtype=np.float64)
@@ -149,10 +152,12 @@ def cpu_baseline_sample(x_plane: np.ndarray, seconds_hint: float = 10.0):
     t1 = time.perf_counter() - t0
     iters = max(1, min(ITERS_, int(seconds_hint / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    oracle.filter(crop, R_, iters)
+    res = oracle.filter(crop, R_, iters, want_gaps=True)
     dt = time.perf_counter() - t0
     mpx = crop.size * iters / dt / 1e6
-    return mpx, oracle.threads(), f"1 plane, 1024x1024 crop of channel 0, r={R_}, {iters} passes, FP64 direct sums"
+    ties = int((oracle.crop(res["gaps"][-1], R_) < 1e-6).sum())
+    return (mpx, oracle.threads(), f"1 plane, 1024x1024 crop of channel 0, r={R_}, {iters} passes, FP64 direct sums",
+            {"count": ties, "pixels": int(crop.size), "pass": iters, "rule": "best two |d_i| within 1e-6 (FP64)"})
 
 
 def run_reference(args):
@@ -278,10 +283,20 @@ def form_batched(dev):
     t_b = _time(batched, 5, warmup=2)
     lat = sorted(osbf.batched_latencies(256))
     t_p = _time(plain, 3, warmup=1)
+    # the tuned layout policy (job order per pass round, CTAs per SM), timed on this batch
+    osbf.autotune_batched(ins, rs, its, outs)
+    pol = osbf.batched_policy(ins, rs, its, outs)
+    t_t = _time(batched, 5, warmup=2)
+    lat_t = sorted(osbf.batched_latencies(256))
     return {"workload": "256 float32 images, H,W~U[64,2048], r in {1,2,3,4,6,8}, passes~U[1,30]",
             "batched_mpix_iter_s": units / t_b / 1e6, "plain_calls_mpix_iter_s": units / t_p / 1e6,
             "batched_over_plain": t_p / t_b, "p50_latency_ms": 1e3 * lat[len(lat) // 2],
             "p99_latency_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "tuned_policy": {"job_order": "by decreasing work" if pol and pol[0] == 1 else "as given",
+                             "ctas_per_sm": pol[1] if pol else None,
+                             "batched_mpix_iter_s": units / t_t / 1e6,
+                             "p50_latency_ms": 1e3 * lat_t[len(lat_t) // 2],
+                             "p99_latency_ms": 1e3 * lat_t[min(len(lat_t) - 1, int(0.99 * len(lat_t)))]},
             "total_pixel_iters": units}
 
 
@@ -298,6 +313,8 @@ def form_precision(dev):
     res = {"workload": "1x3x4320x7680, r=4, 30 passes, sigma 0.03"}
     y0, x0, s = H // 2, W // 2, 48  # sampled output region of plane 0
     ref = None
+    maps32 = None
+    FW = W + 2 * r
     for name, dt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
         xin = x32 if name == "f32" else synth.round_to_storage(x32, name)
         xt = torch.from_numpy(xin).to(dev).to(dt)
@@ -305,12 +322,22 @@ def form_precision(dev):
         t = _time(lambda: osbf.filter(xt, r, it, out=out), 5)
         got = out[0, 0, y0:y0 + s, x0:x0 + s].float().cpu().numpy()
         res[name] = {"mpix_iter_s": 3 * H * W * it / t / 1e6}
+        # selection maps of every pass (not timed): flips against the float32 run
+        maps = torch.empty(osbf.maps_shape(xt, r, it), dtype=torch.uint8, device=dev)
+        osbf.filter(xt, r, it, maps=maps, out=out)
         if ref is None:
             ref = got
+            maps32 = maps
         else:
             d = np.abs(got - ref)
+            flips = [int((maps[k, ..., :FW] != maps32[k, ..., :FW]).sum()) for k in range(it)]
             res[name].update({"max_abs_diff_vs_f32": float(d.max()), "mean_abs_diff_vs_f32": float(d.mean()),
-                              "diff_sample": f"{s}x{s} at ({y0},{x0}), plane 0"})
+                              "diff_sample": f"{s}x{s} at ({y0},{x0}), plane 0",
+                              "selection_flips_vs_f32": {"total": sum(flips), "pass_1": flips[0],
+                                                         "last_pass": flips[-1],
+                                                         "pixel_passes": 3 * (H + 2 * r) * FW * it}})
+            del maps
+    del maps32
     return res
 
 
@@ -384,20 +411,44 @@ def form_gauss(dev, x):
 
 
 def form_sweep(dev, x):
+    """r x fused depth on the tile kernel (the depth actually run, from the launch count: a
+    requested depth is clamped to the largest whose tile fits shared memory), the strip kernel,
+    and the tuner's choice, at 4096^2 x 3; then a 3 x 256 x 256 image, where launch overheads
+    weigh more and fused passes can win."""
     import torch
 
-    from paper_2108_05021_gb300 import osbf
+    from paper_2108_05021_gb300 import osbf, synth
 
-    out = torch.empty_like(x)
-    rows = []
-    for r in (1, 2, 4, 8, 16):
-        for D in (1, 2, 4, 8):
-            try:
-                t = _time(lambda: osbf.filter(x, r, ITERS_, depth=D, out=out), 5, warmup=2)
-            except osbf.OSBFError:
-                continue
-            rows.append({"r": r, "depth": D, "gpix_iter_s": x.numel() * ITERS_ / t / 1e9})
-    return rows
+    def sweep(xx, radii, tag):
+        out = torch.empty_like(xx)
+        N, C, H, W = xx.shape
+        rows = []
+        for r in radii:
+            for D in (1, 2, 4, 8):
+                try:
+                    t = _time(lambda: osbf.filter(xx, r, ITERS_, depth=D, variant="tile", out=out), 5, warmup=2)
+                except osbf.OSBFError:
+                    continue
+                # depth 1 runs ITERS_ launches (+ a padding launch unless the first pass pads
+                # itself); deeper groups always follow a padding launch
+                launches = osbf.last_launch_count(dev.index)
+                eff = 1 if launches >= ITERS_ else -(-ITERS_ // max(launches - 1, 1))
+                rows.append({"input": tag, "r": r, "kernel": "tile", "depth": D, "depth_run": eff,
+                             "gpix_iter_s": xx.numel() * ITERS_ / t / 1e9})
+            if r <= 8:
+                t = _time(lambda: osbf.filter(xx, r, ITERS_, variant="strip", out=out), 5, warmup=2)
+                rows.append({"input": tag, "r": r, "kernel": "strip", "depth": 1, "depth_run": 1,
+                             "gpix_iter_s": xx.numel() * ITERS_ / t / 1e9})
+            osbf.autotune(torch.float32, N * C, H, W, r, ITERS_, device=dev.index)
+            d, v = osbf.tuned(torch.float32, N * C, H, W, r, device=dev.index)
+            t = _time(lambda: osbf.filter(xx, r, ITERS_, out=out), 5, warmup=2)
+            rows.append({"input": tag, "r": r, "kernel": f"tuned ({v})", "depth": d, "depth_run": d,
+                         "gpix_iter_s": xx.numel() * ITERS_ / t / 1e9})
+            osbf.set_tuned(torch.float32, N * C, H, W, r, 1, "tile", device=dev.index)  # back to the default
+        return rows
+
+    small = torch.from_numpy(synth.piecewise_stack(1, 3, 256, 256, seed=52, sigma=0.05)).to(dev)
+    return sweep(x, (1, 2, 4, 8, 16), "1x3x4096x4096") + sweep(small, (1, 2, 4), "1x3x256x256")
 
 
 def main():
@@ -407,6 +458,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--depth", type=int, default=0, help="fused passes per launch (0 = library choice)")
+    ap.add_argument("--variant", default="auto", choices=["auto", "tile", "strip"],
+                    help="float32 single-pass kernel (profiling runs; the default is the library's choice)")
     ap.add_argument("--r", type=int, default=R_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -447,7 +500,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        osbf.filter(x, r, ITERS_, depth=args.depth, out=out)
+        osbf.filter(x, r, ITERS_, depth=args.depth, out=out, variant=args.variant)
 
     for _ in range(args.warmup):
         step()
@@ -480,11 +533,11 @@ def main():
 
     def timed(iters_):
         for _ in range(2):
-            osbf.filter(x, r, iters_, depth=args.depth, out=out)
+            osbf.filter(x, r, iters_, depth=args.depth, out=out, variant=args.variant)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(nrep):
-            osbf.filter(x, r, iters_, depth=args.depth, out=out)
+            osbf.filter(x, r, iters_, depth=args.depth, out=out, variant=args.variant)
         b.record(stream)
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / nrep
@@ -496,7 +549,7 @@ def main():
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_PER_LAUNCH if r == R_ and args.depth in (0, 1) else None,
+                "traffic": TRAFFIC_PER_LAUNCH if r == R_ and args.depth in (0, 1) and args.variant != "strip" else None,
                 "peak_source": peak_kind, "kernel": "osbf_fwd2 (forward tile kernel, frame to frame, tensor stores)",
                 "bytes_per_launch": bytes_per_launch, "launches_per_step": launches_per_step,
                 "launch_ms": launch_ms, "launch_ms_method": "CUDA events: (30-pass call - 2-pass call) / 28",
@@ -527,15 +580,16 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline_sample(x_np[0, 0])
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v, cores, sample, ties = cpu_baseline_sample(x_np[0, 0])
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, "near_ties": ties}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "N": N_, "C": C_, "H": H_, "W": W_, "r": r, "iters": ITERS_,
-                           "depth": args.depth or "library", "l2": "inputs (201 MB) exceed L2; no flush",
+                           "depth": args.depth or "library", "kernel": args.variant if args.variant != "auto" else "library",
+                           "l2": "inputs (201 MB) exceed L2; no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "forms": forms}
