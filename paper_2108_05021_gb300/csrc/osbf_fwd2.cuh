@@ -71,7 +71,9 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     // last segment reads up to SW + 2R + 3 columns past its start
     const int xs_last = ((L.RW0 - 2 * R + SW - 1) / SW - 1) * SW;
     L.PU = xs_last + SW + 2 * R + 4;
-    if (L.PU < L.RW0 + 8) L.PU = L.RW0 + 8;
+    // fused passes also write intermediate rows up to 6 columns past the region; single-pass
+    // (direct) kernels only read, up to column xs_last + SW + 2R + 3
+    if (!direct && L.PU < L.RW0 + 8) L.PU = L.RW0 + 8;
     while (L.PU % 8 != 4) ++L.PU;
     L.P2 = L.PU;  // float row pitch of the column-sum field A (same conflict-free pitch)
     L.BX = sizeof(T) == 4 ? L.PU : round_up(L.PU, 8);
