@@ -624,9 +624,17 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
             if ((unsigned)dx < (unsigned)g.lx) {
                 const int dy0 = g.fy0 - g.oy + rbk * 32;
                 const int nr = g.RHo - rbk * 32 < 32 ? g.RHo - rbk * 32 : 32;
-                for (int j = 0; j < nr; ++j)
-                    if ((unsigned)(dy0 + j) < (unsigned)g.ly)
-                        gdst[(long long)(dy0 + j) * gpitch + dx] = from_f<T>(xst[j * kOutPitch + lane + MO]);
+                const float *src = xst + lane + MO;
+                if (nr == 32 && dy0 >= 0 && dy0 + 32 <= g.ly) {
+                    // every row of the segment lies inside the destination: no per-row checks
+                    T *q = gdst + (long long)dy0 * gpitch + dx;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j, q += gpitch) *q = from_f<T>(src[j * kOutPitch]);
+                } else {
+                    for (int j = 0; j < nr; ++j)
+                        if ((unsigned)(dy0 + j) < (unsigned)g.ly)
+                            gdst[(long long)(dy0 + j) * gpitch + dx] = from_f<T>(src[j * kOutPitch]);
+                }
             }
             __syncwarp();  // the next segment reuses the buffer
         }
@@ -636,9 +644,16 @@ __device__ __forceinline__ void pass_h2(const float *__restrict__ Uin, int pu_in
             if (mplane != nullptr && (unsigned)fx < (unsigned)g.FW) {
                 const int fy0 = g.fy0 + rbk * 32;
                 const int nr = g.RHo - rbk * 32 < 32 ? g.RHo - rbk * 32 : 32;
-                for (int j = 0; j < nr; ++j)
-                    if ((unsigned)(fy0 + j) < (unsigned)g.FH)
-                        mplane[(long long)(fy0 + j) * g.MP + fx] = mst[j * kMapPitch + lane + MO];
+                const uint8_t *src = mst + lane + MO;
+                if (nr == 32 && fy0 >= 0 && fy0 + 32 <= g.FH) {
+                    uint8_t *q = mplane + (long long)fy0 * g.MP + fx;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j, q += g.MP) *q = src[j * kMapPitch];
+                } else {
+                    for (int j = 0; j < nr; ++j)
+                        if ((unsigned)(fy0 + j) < (unsigned)g.FH)
+                            mplane[(long long)(fy0 + j) * g.MP + fx] = src[j * kMapPitch];
+                }
             }
             __syncwarp();  // the next segment reuses the buffer
         }
