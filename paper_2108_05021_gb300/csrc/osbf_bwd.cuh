@@ -302,9 +302,16 @@ __global__ void __launch_bounds__(NT, R <= 8 ? 3 : 2)
                         make_float4(keep[4 * c], keep[4 * c + 1], keep[4 * c + 2], keep[4 * c + 3]);
                 __syncwarp();
                 const int fx = tx0 + warp * SW + lane;
-                if ((unsigned)fx < (unsigned)p.FW)
-                    for (int j = 0; j < TH; ++j)
-                        if (ty0 + j < p.FH) gplane[(long long)(ty0 + j) * p.dst_pitch + fx] = stg[j * kStagePitch + lane];
+                if ((unsigned)fx < (unsigned)p.FW) {
+                    if (ty0 + TH <= p.FH) {  // the tile's rows all lie in the frame: no per-row checks
+                        float *q = gplane + (long long)ty0 * p.dst_pitch + fx;
+#pragma unroll
+                        for (int j = 0; j < TH; ++j, q += p.dst_pitch) *q = stg[j * kStagePitch + lane];
+                    } else {
+                        for (int j = 0; j < TH; ++j)
+                            if (ty0 + j < p.FH) gplane[(long long)(ty0 + j) * p.dst_pitch + fx] = stg[j * kStagePitch + lane];
+                    }
+                }
             }
             // the next tile's pass V writes (F1, F2) after the barrier at the top of the loop
         }
