@@ -51,9 +51,9 @@ WORKLOAD = "osbf forward, 1x3x4096x4096 float32, r=8, 30 passes, piecewise-const
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one frame-to-frame launch of the headline workload's tile
-# kernel (tensor stores), from one ncu capture of that launch: 204.4 MB read + 160.8 MB
-# written (reset to None whenever that kernel changes)
-TRAFFIC_PER_LAUNCH = 365.2e6
+# kernel (early loads, 32-byte register stores), from one ncu capture of that launch:
+# 204.8 MB read + 161.1 MB written (reset to None whenever that kernel changes)
+TRAFFIC_PER_LAUNCH = 365.9e6
 
 
 def hbm_peak():
@@ -550,7 +550,7 @@ def main():
     peak, peak_kind = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_LAUNCH if r == R_ and args.depth in (0, 1) and args.variant != "strip" else None,
-                "peak_source": peak_kind, "kernel": "osbf_fwd2 (forward tile kernel, frame to frame, tensor stores)",
+                "peak_source": peak_kind, "kernel": "osbf_fwd2 (forward tile kernel, frame to frame, early loads, 32-byte register stores)",
                 "bytes_per_launch": bytes_per_launch, "launches_per_step": launches_per_step,
                 "launch_ms": launch_ms, "launch_ms_method": "CUDA events: (30-pass call - 2-pass call) / 28",
                 "hbm_roofline_equiv_mpix_iter_s": peak * 1e9 / 8.0 / 1e6}

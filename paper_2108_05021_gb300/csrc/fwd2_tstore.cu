@@ -11,8 +11,9 @@ cudaError_t launch_fwd2_tstore(int R, bool fast, const CUtensorMap &src, const C
     switch (R) {
 #define OSBF_CASE(RR)                                                                                   \
     case RR:                                                                                            \
-        if (padin && !fast)                                                                             \
-            return v2::launch_fwd2<float, RR, false, false, true, false, true, false, true>(src, p, grid, s, &dmap); \
+        if (padin)                                                                                      \
+            return fast ? v2::launch_fwd2<float, RR, false, false, true, true, true, false, true>(src, p, grid, s, &dmap) \
+                        : v2::launch_fwd2<float, RR, false, false, true, false, true, false, true>(src, p, grid, s, &dmap); \
         return fast ? v2::launch_fwd2<float, RR, false, false, true, true, true>(src, p, grid, s, &dmap) \
                     : v2::launch_fwd2<float, RR, false, false, true, false, true>(src, p, grid, s, &dmap);
         OSBF_CASE(4) OSBF_CASE(8) OSBF_CASE(12) OSBF_CASE(16)

@@ -35,6 +35,7 @@ struct osbf_ctx {
     unsigned int *err_word = nullptr;                // device: bit 0 = a bounded device wait gave up
     unsigned long long wait_ns = 0;                  // bound of the batched dependency wait (0 = default)
     int call_variant = 0;                            // forward kernel of the current call (osbf_variant)
+    int call_fast = 0;                               // the current call runs the fast approximation
 };
 
 // implemented in osbf_bwd_api.cu / osbf_batched.cu
@@ -255,6 +256,10 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
                                       ((uintptr_t)gl.dst % (st == Storage::F32 ? 16 : 8)) == 0);
     const bool direct = Dg == 1 && gl.tie == 0 && out_ok;
+    if (gl.fast && (!direct || st != Storage::F32 || gl.variant == 2)) {
+        *what = "the fast approximation runs single float32 passes written from registers";
+        return cudaErrorInvalidValue;
+    }
     // float32 single passes at r % 4 == 0 (no maps) from frame to frame: results leave
     // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
     // stores (the last pass, into the cropped output, stages its rows instead, on the
@@ -349,14 +354,25 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
         return cudaErrorInvalidValue;
     }
     p.ntiles = (int)ntiles;
-    int occ = tstore ? occupancy_fwd2_tstore(r, false)
+    // frame-to-frame passes of the tensor-store family at r >= 8 issue the next tile's load
+    // before pass H and store from registers, 32 bytes at a time (same arithmetic, so the
+    // same results bit for bit): the frame's row pitch and base lie on 32 bytes
+    // (not for the fast approximation: with fewer instructions per pixel its passes are
+    // bound by shared-memory throughput, which the 32-byte register stores load more than
+    // the tensor stores do)
+    const bool early = tstore && !last_out && !gl.src_is_image && !gl.fast && fwd2_early_radius(r) &&
+                       gl.dst_pitch % 8 == 0 && ((uintptr_t)gl.dst & 31) == 0;
+    int occ = early ? occupancy_fwd2_early(r, false) : tstore ? occupancy_fwd2_tstore(r, gl.fast != 0)
+                     : gl.fast ? occupancy_fwd2_fast(r, gl.maps != nullptr)
                      : (st == Storage::F16    ? occupancy_fwd2_f16(r, gl.tie != 0, gl.maps != nullptr, direct, Dg)
                         : st == Storage::BF16 ? occupancy_fwd2_bf16(r, gl.tie != 0, gl.maps != nullptr, direct, Dg)
                                               : occupancy_fwd2_f32(r, gl.tie != 0, gl.maps != nullptr, direct, Dg));
     if (occ < 1) occ = 1;
     const long long g = (long long)occ * gl.sms;
     const int grid = (int)(g < ntiles ? g : ntiles);
-    if (tstore) return launch_fwd2_tstore(r, false, map, dmap, p, grid, s, gl.src_is_image != 0);
+    if (early) return launch_fwd2_early(r, false, map, p, grid, s);
+    if (tstore) return launch_fwd2_tstore(r, gl.fast != 0, map, dmap, p, grid, s, gl.src_is_image != 0);
+    if (gl.fast) return launch_fwd2_fast(r, gl.maps != nullptr, map, p, grid, s);
     switch (st) {
     case Storage::F16: return launch_fwd2_f16(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
     case Storage::BF16: return launch_fwd2_bf16(r, gl.tie != 0, gl.maps != nullptr, direct, map, p, grid, s);
@@ -379,8 +395,13 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     const size_t frame_bytes = fes * (size_t)P * FH * FWp;
     const int MP = maps_pitch(FW);
 
-    int D = depth > 0 ? depth : 0;
-    int variant = ctx->call_variant;
+    const bool fast = ctx->call_fast != 0;
+    int D = fast ? 1 : depth > 0 ? depth : 0;
+    int variant = fast ? (int)OSBF_VARIANT_TILE : ctx->call_variant;
+    // the fast approximation writes the cropped output from registers only where its rows
+    // hold aligned 4-vectors (r % 4 == 0, W % 4 == 0); otherwise its last pass writes a
+    // frame and a crop follows
+    const bool fast_crop = fast && !out_is_frame && !(W % 4 == 0 && r % 4 == 0 && ((uintptr_t)out & 15) == 0);
     if (D == 0) {
         // the tuned choice (osbf_autotune) applies when the caller fixed neither the depth
         // nor the kernel
@@ -497,11 +518,12 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         gl.sms = ctx->sms;
         gl.variant = variant;
         gl.src_is_image = pad_fused && passes == 0;
+        gl.fast = fast ? 1 : 0;
         int nxt = -1;
-        if (last && !out_is_frame) {
+        if (last && !out_is_frame && !fast_crop) {
             gl.dst = out;
             gl.dst_is_output = 1;
-        } else if (last) {
+        } else if (last && out_is_frame) {
             gl.dst = out;
             gl.dst_pitch = out_pitch;
         } else {
@@ -521,6 +543,11 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
             src = fb[nxt];
             src_pitch = FWp;
         }
+    }
+    if (fast_crop) {
+        cudaError_t e = launch_crop_f32((const float *)fb[cur], (float *)out, P, H, W, r, FWp, s);
+        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "crop launch failed: %s", cudaGetErrorString(e));
+        ctx->last_launches += 1;
     }
     return OSBF_OK;
 }
@@ -862,92 +889,13 @@ osbf_status osbf_filter_fast(osbf_ctx *ctx, const float *in, float *out, int N, 
         }
         return OSBF_OK;
     }
-    const size_t frame_bytes = 4 * (size_t)P * FH * FWp;
-    for (int k = 0; k < 2; ++k) {
-        osbf_status e = ensure(ctx, &ctx->frames[k], &ctx->frame_bytes[k], frame_bytes);
-        if (e) return e;
-    }
-    float *frame[2] = {(float *)ctx->frames[0], (float *)ctx->frames[1]};
-    cudaError_t e = launch_pad_replicate(Storage::F32, in, frame[0], (int)P, H, W, r, FH, FW, FWp, s);
-    if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "pad launch failed: %s", cudaGetErrorString(e));
-    ctx->last_launches += 1;
-    const v2::Layout2 L = v2::make_layout2<float>(r, 1, true);
-    const int shift = (4 - r % 4) % 4;  // tile k starts at column k*TW - shift: the TMA box starts on 16 bytes
-    // r % 4 == 0 without maps: frame-to-frame passes store through per-warp tensor stores
-    const bool tstore_ok = r % 4 == 0 && !maps;
-    int occ_ts = tstore_ok ? occupancy_fwd2_tstore(r, true) : 0;
-    int occ = occupancy_fwd2_fast(r, maps != nullptr);
-    if (occ < 1) occ = 1;
-    if (occ_ts < 1) occ_ts = 1;
-    int cur = 0;
-    bool wrote_output = false;
-    for (int pass = 0; pass < iters; ++pass) {
-        // the last pass writes the cropped output from registers when its rows hold 16-byte
-        // aligned 4-vectors; otherwise it writes a frame and the crop follows
-        const bool to_output =
-            pass == iters - 1 && W % 4 == 0 && r % 4 == 0 && ((uintptr_t)out % 16) == 0;
-        CUtensorMap map;
-        if (!encode_frame_map(&map, Storage::F32, frame[cur], FW, FH, (int)P, FWp, L.BX, L.RH0))
-            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame %dx%dx%lld)", FW, FH, P);
-        v2::Fwd2Params p;
-        std::memset(&p, 0, sizeof p);
-        p.H = H;
-        p.W = W;
-        p.FH = FH;
-        p.FW = FW;
-        p.D = 1;
-        p.maps = maps;
-        p.map_pitch = MP;
-        p.map_iter0 = pass;
-        p.map_iter_stride = map_stride;
-        p.map_plane = (long long)FH * MP;
-        p.err = ctx->err_word;
-        int ty0 = 0, ty1 = (FH - 1) / v2::TH, tx0 = 0, tx1 = (FW - 1 + shift) / v2::TW;
-        if (to_output) {
-            p.dst = out;
-            p.dst_is_output = 1;
-            p.dst_plane = (long long)H * W;
-            p.dst_pitch = W;
-            if (!maps) {  // with maps, every frame pixel's selection is recorded
-                ty0 = r / v2::TH;
-                ty1 = (r + H - 1) / v2::TH;
-                tx0 = (r + shift) / v2::TW;
-                tx1 = (r + W - 1 + shift) / v2::TW;
-            }
-        } else {
-            p.dst = frame[1 - cur];
-            p.dst_plane = (long long)FH * FWp;
-            p.dst_pitch = FWp;
-        }
-        p.ty_off = ty0;
-        p.tx_off = tx0;
-        p.tx_shift = shift;
-        p.tiles_x = tx1 - tx0 + 1;
-        p.tiles_y = ty1 - ty0 + 1;
-        const bool tstore = tstore_ok && !to_output;
-        CUtensorMap dmap;
-        if (tstore && !encode_store_map(&dmap, frame[1 - cur], FW, FH, (int)P, FWp))
-            return fail(ctx, OSBF_ECUDA, "cuTensorMapEncodeTiled failed (frame store map)");
-        const long long ntiles = (long long)p.tiles_x * p.tiles_y * P;
-        if (ntiles > 0x7fffffffLL) return fail(ctx, OSBF_EUNSUPPORTED, "too many tiles");
-        p.ntiles = (int)ntiles;
-        const long long gmax = (long long)(tstore ? occ_ts : occ) * ctx->sms;
-        const int grid = (int)(gmax < ntiles ? gmax : ntiles);
-        e = tstore ? launch_fwd2_tstore(r, true, map, dmap, p, grid, s)
-                   : launch_fwd2_fast(r, maps != nullptr, map, p, grid, s);
-        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "fast forward launch failed: %s", cudaGetErrorString(e));
-        ctx->last_launches += 1;
-        if (to_output)
-            wrote_output = true;
-        else
-            cur = 1 - cur;
-    }
-    if (!wrote_output) {
-        e = launch_crop_f32(frame[cur], out, (int)P, H, W, r, FWp, s);
-        if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "crop launch failed: %s", cudaGetErrorString(e));
-        ctx->last_launches += 1;
-    }
-    return OSBF_OK;
+    // the float32 forward's launch plan (padding first pass, output-aligned last pass,
+    // shared tile origins for the plain and the map-writing calls) with the fast kernels
+    ctx->call_fast = 1;
+    const osbf_status st = osbf_forward_run(ctx, in, 0, 0, out, 0, 0, (int)P, H, W, r, iters, OSBF_F32, 1, 0, maps, 0,
+                                            map_stride, s);
+    ctx->call_fast = 0;
+    return st;
 }
 
 osbf_status osbf_filter_backward(osbf_ctx *ctx, const float *grad_out, float *grad_in, const uint8_t *maps, int N,

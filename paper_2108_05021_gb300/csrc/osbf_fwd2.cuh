@@ -42,6 +42,7 @@ struct Layout2 {
     int off_st;  // tensor-store staging: NT/32 buffers of 32 x 32 floats, placed 1024-aligned at run time
     int off_ms;  // single-pass map staging: NT/32 buffers of 32 rows x kMapPitch bytes
     int off_xs;  // single-pass result staging: NT/32 buffers of 32 rows x kOutPitch floats
+    int off_uc;  // EARLY: copy of the tile's TH centre rows of U^0 (row pitch PU), made by pass V
 };
 
 __host__ __device__ inline int align128(int b) { return (b + 127) & ~127; }
@@ -57,7 +58,7 @@ constexpr int kOutPitch = 36;
 
 template <typename T>
 __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = false, bool tstore = false,
-                                                bool mstage = false, bool xstage = false) {
+                                                bool mstage = false, bool xstage = false, bool early = false) {
     Layout2 L;
     const int xa = 16 / (int)sizeof(T) < 4 ? 4 : 16 / (int)sizeof(T);
     L.EY = D * R;
@@ -97,6 +98,8 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     if (mstage) off = align128(off + (NT / 32) * 32 * kMapPitch);
     L.off_xs = off;
     if (xstage) off = align128(off + (NT / 32) * 32 * kOutPitch * 4);
+    L.off_uc = off;
+    if (early) off = align128(off + TH * L.PU * 4);
     L.bytes = off + 16;  // + mbarrier
     return L;
 }
@@ -241,11 +244,14 @@ template <> __device__ __forceinline__ void cvt_store4<__nv_bfloat16>(__nv_bfloa
 // ----------------------------------------------------------------------------------
 // pass V on column pairs: a(y) = sum_{y-R..y} U(., x), stored at A[y - R] for region rows
 // y in [R, RH).  NRH > 0: the row count is a compile-time constant (single-pass
-// launches), so the sweep is fully unrolled.
+// launches), so the sweep is fully unrolled.  UC (NRH > 0): the region's centre rows
+// [R, R + TH) -- the pixels pass H filters -- are also copied to Uc (row pitch pc), so the
+// input buffer is dead once pass V ends.
 // ----------------------------------------------------------------------------------
-template <int R, int NRH>
+template <int R, int NRH, bool UC = false>
 __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float *__restrict__ A, int pa, int RH_rt,
-                                        int RW) {
+                                        int RW, float *__restrict__ Uc = nullptr, int pc = 0) {
+    static_assert(!UC || NRH > 0, "the centre-row copy: unrolled sweeps");
     constexpr int P = R + 1;
     const int npairs = (RW + 1) >> 1;
     for (int item = threadIdx.x; item < npairs; item += NT) {
@@ -282,6 +288,7 @@ __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, flo
             for (int s = 0; s < NR; ++s) {
                 const float2 v = q[s % LA];
                 if (s + LA < NR) q[s % LA] = *reinterpret_cast<const float2 *>(col + (s + LA) * pu);
+                if (UC && s >= R && s < R + TH) *reinterpret_cast<float2 *>(Uc + (s - R) * pc + c) = v;
                 update(v, s % P);
                 if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
             }
@@ -700,15 +707,22 @@ __device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &
 // zeros beyond it, and tiles touching its border then set every frame cell outside the
 // image to its nearest image cell (the appendix's replicate pad), which always lies in
 // the same box -- no separate padding pass.
+// EARLY (float32 frame to frame, R % 4 == 0, no maps): pass V copies the centre rows that
+// pass H reads, so the next tile's load is issued before pass H instead of after it and
+// lands while pass H runs; results leave by 32-byte register stores (the frame's columns
+// at a segment start lie on 32 bytes: no grid shift, a 32-float row pitch), which frees
+// the tensor-store staging for the copy.
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false, bool PADIN = false>
-__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !XSTAGE ? 4 : 3) : 2)
+          bool XSTAGE = false, bool PADIN = false, bool EARLY = false>
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !XSTAGE && !EARLY ? 4 : 3) : 2)
     osbf_fwd2(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dmap, const Fwd2Params p) {
     static_assert(!TSTORE || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0), "tensor stores: float32, R % 4 == 0");
     static_assert(!PADIN || TSTORE, "the padding first pass: the tensor-store kernel");
+    static_assert(!EARLY || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0 && !TSTORE && !XSTAGE),
+                  "early loads: float32 frame to frame, R % 4 == 0, no maps");
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
-    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE, EARLY);
     float *sbase = nullptr;  // TSTORE staging, 1024-aligned (the 128-byte swizzle repeats every 1024 bytes)
     if (TSTORE) {
         const uint32_t a = smem_u32(smem2 + L.off_st);
@@ -824,11 +838,19 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
             const int puin = j == 1 ? pu0 : L.PU;
             float *Uout = (j & 1) ? Ua : Ub;
             const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
-            if (DIRECT)
+            float *Uc = reinterpret_cast<float *>(smem2 + L.off_uc);
+            if (EARLY) {
+                pass_v2<R, TH + 2 * R, true>(Uin, puin, A, L.P2, RH, RW, Uc, L.PU);
+                __syncthreads();
+                prefetch(tile);  // the input box is dead: its next load overlaps pass H
+                prefetched = true;
+            } else if (DIRECT) {
                 pass_v2<R, TH + 2 * R>(Uin, puin, A, L.P2, RH, RW);
-            else
+                __syncthreads();
+            } else {
                 pass_v2<R, 0>(Uin, puin, A, L.P2, RH, RW);
-            __syncthreads();
+                __syncthreads();
+            }
             Geom2 g;
             g.RHo = RH - 2 * R;
             g.RWo = RW - 2 * R;
@@ -856,9 +878,9 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE>(
-                Uin, puin, R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g, mplane, sbase, &dmap, smem2 + L.off_ms,
-                reinterpret_cast<float *>(smem2 + L.off_xs));
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, false, EARLY>(
+                EARLY ? Uc : Uin, EARLY ? L.PU : puin, EARLY ? 0 : R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g,
+                mplane, sbase, &dmap, smem2 + L.off_ms, reinterpret_cast<float *>(smem2 + L.off_xs));
             __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
@@ -905,11 +927,11 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
 
 // dmap: the destination's tensor map (read only by TSTORE kernels; any map otherwise)
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false, bool PADIN = false>
+          bool XSTAGE = false, bool PADIN = false, bool EARLY = false>
 cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, cudaStream_t stream,
                         const CUtensorMap *dmap = nullptr) {
-    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, PADIN>;
+    const Layout2 L = make_layout2<T>(R, p.D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE, EARLY);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, PADIN, EARLY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, L.bytes, stream>>>(src, dmap ? *dmap : src, p);
@@ -917,10 +939,10 @@ cudaError_t launch_fwd2(const CUtensorMap &src, const Fwd2Params &p, int grid, c
 }
 
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
-          bool XSTAGE = false>
+          bool XSTAGE = false, bool EARLY = false>
 int occupancy_fwd2(int D) {
-    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE);
-    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE>;
+    const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE, EARLY);
+    auto kern = osbf_fwd2<T, R, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, false, EARLY>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, L.bytes) != cudaSuccess) return 0;

@@ -48,6 +48,15 @@ int occupancy_fwd2_fast(int R, bool maps);
 cudaError_t launch_fwd2_tstore(int R, bool fast, const CUtensorMap &src, const CUtensorMap &dmap,
                                const v2::Fwd2Params &p, int grid, cudaStream_t s, bool padin = false);
 int occupancy_fwd2_tstore(int R, bool fast);
+// single-pass float32 frame-to-frame launches that issue the next tile's load before pass H
+// (R % 4 == 0, paper tie order, no maps; 32-byte register stores into a frame whose row
+// pitch is a multiple of 32 floats)
+cudaError_t launch_fwd2_early(int R, bool fast, const CUtensorMap &src, const v2::Fwd2Params &p, int grid,
+                              cudaStream_t s);
+int occupancy_fwd2_early(int R, bool fast);
+// The radii whose frame-to-frame passes take the early-load kernel: at r = 8, 12, 16 it is
+// 2-6 % faster than the tensor-store kernel on 4096^2 x 3 planes; at r = 4 0.7 % slower.
+inline bool fwd2_early_radius(int r) { return r % 4 == 0 && r >= 8; }
 
 // A float32 destination for tensor stores: P planes of H rows x W elements (row pitch
 // `pitch` elements), 32 x 32 boxes staged with the 128-byte swizzle.
@@ -76,6 +85,7 @@ struct GroupLaunch {
     int sms = 0;
     int variant = 0;  // forward kernel: 0 = library choice, 1 = tile kernel, 2 = streaming strip kernel
     int src_is_image = 0;  // src is the caller's unpadded image (row pitch W): the first pass pads it itself
+    int fast = 0;  // the fast approximation (float32, paper tie order, single passes written from registers)
 };
 cudaError_t launch_group(const GroupLaunch &g, cudaStream_t s, const char **what);
 

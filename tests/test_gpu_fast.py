@@ -79,3 +79,16 @@ def test_fast_trivial_and_status_codes():
     assert e.value.status_name == "OSBF_EINVAL"
     with pytest.raises(TypeError):
         osbf.filter_fast(x.half(), 2, 1)
+
+
+def test_fast_launch_plan():
+    """The fast approximation shares the float32 forward's launch plan: at r % 4 == 0 and
+    W % 4 == 0 the first pass pads the image itself and the last pass writes the cropped
+    output (one launch per pass); otherwise a padding launch precedes the passes and a crop
+    follows them.  Both plans against the oracle."""
+    for (H, W, r, launches) in [(200, 512, 8, 4), (200, 302, 3, 4 + 2)]:
+        x_np = synth.piecewise_stack(1, 2, H, W, seed=H + r, sigma=0.05)
+        x = torch.from_numpy(x_np).to(DEV)
+        osbf.filter_fast(x, r, 4)
+        assert osbf.last_launch_count(0) == launches, (H, W, r)
+        check(x_np, r, 4)
