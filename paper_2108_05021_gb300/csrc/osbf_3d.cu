@@ -51,7 +51,10 @@ __global__ void pad3d_kernel(const float *__restrict__ in, float *__restrict__ f
         dst[fx] = src[min(max(fx - R, 0), v.W - 1)];
 }
 
-// z-pass: thread = one (plane, y, x) column of the frame; ring over depths z-R..z+R
+// z-pass: thread = one (plane, y, x) column of the frame; ring over depths z-R..z+R.  The
+// depths entering during a ring period (Q steps) are loaded a whole period ahead, so Q
+// loads per thread are in flight while the current period is summed (one load per step,
+// used at once, left the kernel waiting on memory latency).
 template <int R>
 __global__ void zpass_kernel(const float *__restrict__ U, float *__restrict__ Zm, float *__restrict__ Zp, Vol v) {
     constexpr int Q = 2 * R + 1;
@@ -65,13 +68,26 @@ __global__ void zpass_kernel(const float *__restrict__ U, float *__restrict__ Zm
 #pragma unroll
     for (int k = 0; k < R; ++k)  // depths 0..R-1 enter ahead of the first output
         if (k < v.FD) ring[k % Q] = U[base + k * zs];
+    // nxt[k]: the depth entering at step k of the next period (z0 + k + R), zero past the volume
+    float nxt[Q];
+    auto load_period = [&](int z0) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int zn = z0 + k + R;
+            nxt[k] = zn < v.FD ? __ldg(U + base + (long long)zn * zs) : 0.f;
+        }
+    };
+    load_period(0);
     for (int z0 = 0; z0 < v.FD; z0 += Q) {
+        float cur[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) cur[k] = nxt[k];
+        if (z0 + Q < v.FD) load_period(z0 + Q);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int z = z0 + k;
             if (z < v.FD) {
-                const int zn = z + R;  // depth entering the ring; slot (k + R) % Q, the one z - R - 1 left
-                ring[(k + R) % Q] = zn < v.FD ? U[base + (long long)zn * zs] : 0.f;
+                ring[(k + R) % Q] = cur[k];  // depth z + R takes the slot depth z - R - 1 left
                 float sm = ring[k], sp = ring[k];
 #pragma unroll
                 for (int j = 1; j <= R; ++j) {
@@ -209,9 +225,17 @@ __global__ void __launch_bounds__(NT) yx_kernel(const __grid_constant__ CUtensor
         for (int k = 0; k < P; ++k) rf[f][k] = lh[f][k] = 0.f;
     float ucol[P];
     const int fy = ty0 + y;
+    // the sweep runs in blocks of UN steps, a multiple of the ring period and of the 4-step
+    // load group, so ring slots and vector lanes stay static while the code stays within
+    // the instruction cache (a fully unrolled sweep stalled on instruction fetch)
+    constexpr int UN = (P % 4 == 0) ? P : (P % 2 == 0 ? 2 * P : 4 * P);
+#pragma unroll 1
+    for (int t0 = 0; t0 < NS; t0 += UN) {
 #pragma unroll
-    for (int t = 0; t < NS; ++t) {
-        const int k = t % P, j = t & 3;
+    for (int i = 0; i < UN; ++i) {
+        const int t = t0 + i;
+        if (t >= NS) break;
+        const int k = i % P, j = i & 3;
         if (j == 0) {
             const int g = t >> 2;
             vau = gau[g];
@@ -299,6 +323,7 @@ __global__ void __launch_bounds__(NT) yx_kernel(const __grid_constant__ CUtensor
                 if (MAPS) q.maps[(((long long)p * v.FD + z) * v.FH + fy) * v.FW + fx] = (uint8_t)m;
             }
         }
+    }
     }
 }
 
