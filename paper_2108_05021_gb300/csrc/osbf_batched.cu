@@ -79,19 +79,30 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
+// The region loads issue kLoadBatch loads per thread before storing any of them: a load
+// stored at once into shared memory leaves the thread waiting a full L2 round trip per
+// element.
+constexpr int kLoadBatch = 16;
+
 // Pass 0's region: the replicate-padded input (clamped reads), zero outside the frame.
-// One flat loop over the box's elements (row-major, consecutive threads on consecutive
-// columns).
+// Consecutive threads take consecutive elements of the row-major box.
 __device__ void load_padded_input(const Job &jb, const v2::Layout2 &L, float *box, int ty0, int tx0) {
     const int fy0 = ty0 - L.EY, fx0 = tx0 - L.EX;
     const int n = L.RH0 * L.BX;
-    for (int e = threadIdx.x; e < n; e += v2::NT) {
-        const int y = e / L.BX, x = e - y * L.BX;
-        const int fy = fy0 + y, fx = fx0 + x;
-        float v = 0.f;
-        if ((unsigned)fy < (unsigned)jb.FH && (unsigned)fx < (unsigned)jb.FW)
-            v = jb.in[(long long)min(max(fy - jb.R, 0), jb.H - 1) * jb.W + min(max(fx - jb.R, 0), jb.W - 1)];
-        box[e] = v;
+    for (int e0 = threadIdx.x; e0 < n; e0 += kLoadBatch * v2::NT) {
+        float v[kLoadBatch];
+#pragma unroll
+        for (int i = 0; i < kLoadBatch; ++i) {
+            const int e = e0 + i * v2::NT;
+            const int y = e / L.BX, x = e - y * L.BX;
+            const int fy = fy0 + y, fx = fx0 + x;
+            v[i] = 0.f;
+            if (e < n && (unsigned)fy < (unsigned)jb.FH && (unsigned)fx < (unsigned)jb.FW)
+                v[i] = jb.in[(long long)min(max(fy - jb.R, 0), jb.H - 1) * jb.W + min(max(fx - jb.R, 0), jb.W - 1)];
+        }
+#pragma unroll
+        for (int i = 0; i < kLoadBatch; ++i)
+            if (e0 + i * v2::NT < n) box[e0 + i * v2::NT] = v[i];
     }
 }
 
@@ -104,17 +115,29 @@ __device__ void load_frame_region(const Job &jb, const float *src, const v2::Lay
     const int fy0 = ty0 - L.EY, fx0 = tx0 - L.EX;
     const int nv = L.BX / 4;
     const int n = L.RH0 * nv;
-    for (int e = threadIdx.x; e < n; e += v2::NT) {
-        const int y = e / nv, x = (e - y * nv) * 4;
-        const int fy = fy0 + y, fx = fx0 + x;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned)fy < (unsigned)jb.FH && fx >= 0 && fx < jb.FW) {
-            v = __ldcg(reinterpret_cast<const float4 *>(src + (long long)fy * jb.FWp + fx));
-            if (fx + 1 >= jb.FW) v.y = 0.f;
-            if (fx + 2 >= jb.FW) v.z = 0.f;
-            if (fx + 3 >= jb.FW) v.w = 0.f;
+    for (int e0 = threadIdx.x; e0 < n; e0 += kLoadBatch * v2::NT) {
+        float4 v[kLoadBatch];
+#pragma unroll
+        for (int i = 0; i < kLoadBatch; ++i) {
+            const int e = e0 + i * v2::NT;
+            const int y = e / nv, x = (e - y * nv) * 4;
+            const int fy = fy0 + y, fx = fx0 + x;
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < n && (unsigned)fy < (unsigned)jb.FH && fx >= 0 && fx < jb.FW) {
+                v[i] = __ldcg(reinterpret_cast<const float4 *>(src + (long long)fy * jb.FWp + fx));
+                if (fx + 1 >= jb.FW) v[i].y = 0.f;
+                if (fx + 2 >= jb.FW) v[i].z = 0.f;
+                if (fx + 3 >= jb.FW) v[i].w = 0.f;
+            }
         }
-        *reinterpret_cast<float4 *>(box + y * L.BX + x) = v;
+#pragma unroll
+        for (int i = 0; i < kLoadBatch; ++i) {
+            const int e = e0 + i * v2::NT;
+            if (e < n) {
+                const int y = e / nv, x = (e - y * nv) * 4;
+                *reinterpret_cast<float4 *>(box + y * L.BX + x) = v[i];
+            }
+        }
     }
 }
 
@@ -214,11 +237,11 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
             default: process<8>(jb, g, it.z, bsmem); break;
             }
         }
-        // a fence orders only its own thread's writes: every thread publishes its stores
-        // of this tile before the tile is counted
-        __threadfence();
+        // every thread's stores of this tile precede the barrier; thread 0's fence, which
+        // is cumulative over them, publishes them before the tile is counted
         __syncthreads();
         if (threadIdx.x == 0) {
+            __threadfence();
             const int prev = atomicAdd(p.done + jb.cnt_base + g, 1);
             if (it.w && prev + 1 == jb.ntiles) p.t_done[it.x] = now_ns();
         }
