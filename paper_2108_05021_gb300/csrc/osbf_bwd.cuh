@@ -210,16 +210,18 @@ __device__ __forceinline__ void bwd_pass_h(const float *__restrict__ gb, const f
     }
 }
 
-// Staged stores (r <= 4, where the 32 results per lane fit the register budget): after the
-// barrier that ends pass H, each pass-H warp parks its 32 x 32 results in the dead (F1, F2)
-// field (rows of kStagePitch floats, an odd number of 16-byte chunks) and writes them row
-// by row, a lane per column: 32 consecutive floats per store instruction instead of a
-// 16-byte piece in each of 32 rows.
+// Staged stores (r <= 8): after the barrier that ends pass H, each pass-H warp parks its
+// 32 x 32 results in the dead (F1, F2) field (rows of kStagePitch floats, an odd number of
+// 16-byte chunks) and writes them row by row, a lane per column: 32 consecutive floats per
+// store instruction instead of a 16-byte piece in each of 32 rows.  The 32 results a lane
+// holds fit three CTAs per SM up to r = 4; at r = 5..8 the kernel runs two CTAs per SM
+// with them (faster than three with per-lane stores: 193 -> 216 Gpixel/s at r = 5,
+// 195 -> 205 at r = 8 on 4096^2 x 3).
 constexpr int kStagePitch = 36;
-template <int R> __host__ __device__ constexpr bool bwd_stage() { return R <= 4; }
+template <int R> __host__ __device__ constexpr bool bwd_stage() { return R <= 8; }
 
 template <int R>
-__global__ void __launch_bounds__(NT, R <= 8 ? 3 : 2)
+__global__ void __launch_bounds__(NT, R <= 4 ? 3 : 2)
     osbf_bwd_kernel(const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap mmap,
                     const BwdParams p) {
     extern __shared__ __align__(128) unsigned char bsm[];
