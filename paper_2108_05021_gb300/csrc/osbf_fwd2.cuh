@@ -881,7 +881,9 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
             pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, false, EARLY>(
                 EARLY ? Uc : Uin, EARLY ? L.PU : puin, EARLY ? 0 : R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g,
                 mplane, sbase, &dmap, smem2 + L.off_ms, reinterpret_cast<float *>(smem2 + L.off_xs));
-            __syncthreads();
+            // EARLY: the next load is already out, and the barrier after the next tile's
+            // load wait orders this pass H's reads before the next pass V's writes
+            if (!EARLY) __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
                 prefetched = true;
