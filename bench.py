@@ -52,8 +52,8 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one frame-to-frame launch of the headline workload's tile
 # kernel (early loads, 32-byte register stores), from one ncu capture of that launch:
-# 204.8 MB read + 161.1 MB written (reset to None whenever that kernel changes)
-TRAFFIC_PER_LAUNCH = None
+# 204.9 MB read + 161.0 MB written (reset to None whenever that kernel changes)
+TRAFFIC_PER_LAUNCH = 366.0e6
 
 
 def hbm_peak():
