@@ -95,8 +95,9 @@ def test_radii_ragged_tiles(shape, variant, r):
 @pytest.mark.parametrize("W", [256, 258])
 def test_no_maps_kernels_match_oracle(variant, r, W):
     """The kernels a plain call runs (no maps): frame-to-frame passes at r % 4 == 0 leave
-    through per-warp tensor stores; the last pass writes the cropped output straight from
-    the kernel when W % 4 == 0 (staged rows) and through the shared-memory kernel otherwise.
+    through per-warp tensor stores (r = 4) or the early-load kernel's 32-byte register
+    stores (r >= 8); the last pass writes the cropped output with tensor stores on the
+    output-aligned grid when W % 4 == 0 and through the shared-memory kernel otherwise.
     Their results equal the map-writing run bit for bit (same arithmetic, so the maps run's
     selections are the no-maps run's), and the oracle, hinted with those maps, agrees
     within 1e-5 on every pixel."""
@@ -124,8 +125,9 @@ def test_padding_first_pass(shape, r):
 
 def test_bench_shape_sampled():
     """The benchmark's own workload and launch sequence: 1 x 3 x 4096 x 4096 float32, r = 8,
-    30 passes, the bench's input (seed 0).  The plain call (tensor-store passes, staged last
-    pass) equals the map-writing call bit for bit on the whole output; 32 x 32 regions --
+    30 passes, the bench's input (seed 0).  The plain call (the padding first pass, early-load
+    passes, the tensor-store pass into the output) equals the map-writing call bit for bit
+    on the whole output; 32 x 32 regions --
     the top-left frame corner, a region straddling a tile seam in both axes, an interior
     region and the bottom-right corner -- match the oracle (dependency cone only, hinted
     with the run's maps) within 1e-5."""
