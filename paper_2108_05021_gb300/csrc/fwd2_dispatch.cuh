@@ -13,6 +13,9 @@ namespace osbf {
 
 // direct float32 kernels stage their results per warp and write them a row at a time
 template <typename T> constexpr bool kStage = sizeof(T) == 4;
+// direct 16-bit kernels without maps widen their box in pass V and load the next tile
+// before pass H (osbf_fwd2.cuh, EARLY)
+template <typename T> constexpr bool kEarly = sizeof(T) == 2;
 
 template <typename T, bool APP_MAPS>
 cudaError_t launch_fwd2_t(int R, bool tie_app, bool maps, bool direct, const CUtensorMap &src,
@@ -22,7 +25,7 @@ cudaError_t launch_fwd2_t(int R, bool tie_app, bool maps, bool direct, const CUt
     case RR:                                                                                             \
         if (direct && !tie_app)                                                                          \
             return maps ? v2::launch_fwd2<T, RR, false, true, true, false, false, kStage<T>>(src, p, grid, s) \
-                        : v2::launch_fwd2<T, RR, false, false, true, false, false, kStage<T>>(src, p, grid, s); \
+                        : v2::launch_fwd2<T, RR, false, false, true, false, false, kStage<T>, false, kEarly<T>>(src, p, grid, s); \
         if (tie_app) {                                                                                   \
             if (!maps) return v2::launch_fwd2<T, RR, true, false, false>(src, p, grid, s);               \
             if constexpr (APP_MAPS) return v2::launch_fwd2<T, RR, true, true, false>(src, p, grid, s);   \
@@ -43,7 +46,7 @@ int occupancy_fwd2_t(int R, bool tie_app, bool maps, bool direct, int D) {
     case RR:                                                                              \
         if (direct && !tie_app)                                                           \
             return maps ? v2::occupancy_fwd2<T, RR, false, true, true, false, false, kStage<T>>(D) \
-                        : v2::occupancy_fwd2<T, RR, false, false, true, false, false, kStage<T>>(D); \
+                        : v2::occupancy_fwd2<T, RR, false, false, true, false, false, kStage<T>, kEarly<T>>(D); \
         if (tie_app) {                                                                    \
             if (!maps) return v2::occupancy_fwd2<T, RR, true, false, false>(D);           \
             if constexpr (APP_MAPS) return v2::occupancy_fwd2<T, RR, true, true, false>(D); \

@@ -84,7 +84,7 @@ __host__ __device__ inline Layout2 make_layout2(int R, int D, bool direct = fals
     L.off_in = off;
     off = align128(off + L.in_bytes);
     L.off_uf = off;  // float copy of the input (16-bit storage only)
-    if (sizeof(T) != 4) off = align128(off + L.RH0 * L.PU * 4);
+    if (sizeof(T) != 4 && !early) off = align128(off + L.RH0 * L.PU * 4);
 
     L.off_ab = off;
     off = align128(off + (L.RH0 - R) * L.P2 * 4);
@@ -248,15 +248,28 @@ template <> __device__ __forceinline__ void cvt_store4<__nv_bfloat16>(__nv_bfloa
 // [R, R + TH) -- the pixels pass H filters -- are also copied to Uc (row pitch pc), so the
 // input buffer is dead once pass V ends.
 // ----------------------------------------------------------------------------------
-template <int R, int NRH, bool UC = false>
-__device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, float *__restrict__ A, int pa, int RH_rt,
+// Two neighbouring source elements as floats (the pair starts on an even column).
+template <typename TS> __device__ __forceinline__ float2 ld_pair(const TS *p);
+template <> __device__ __forceinline__ float2 ld_pair<float>(const float *p) {
+    return *reinterpret_cast<const float2 *>(p);
+}
+template <> __device__ __forceinline__ float2 ld_pair<__half>(const __half *p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+template <> __device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+
+// TS: the source's storage type (16-bit sources are widened in registers)
+template <int R, int NRH, bool UC = false, typename TS = float>
+__device__ __forceinline__ void pass_v2(const TS *__restrict__ U, int pu, float *__restrict__ A, int pa, int RH_rt,
                                         int RW, float *__restrict__ Uc = nullptr, int pc = 0) {
     static_assert(!UC || NRH > 0, "the centre-row copy: unrolled sweeps");
     constexpr int P = R + 1;
     const int npairs = (RW + 1) >> 1;
     for (int item = threadIdx.x; item < npairs; item += NT) {
         const int c = item * 2;
-        const float *col = U + c;
+        const TS *col = U + c;
         float2 *acol = reinterpret_cast<float2 *>(A + c);
         float2 ring[P];
 #pragma unroll
@@ -283,11 +296,11 @@ __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, flo
             float2 q[LA];
 #pragma unroll
             for (int i = 0; i < LA; ++i)
-                q[i] = i < NR ? *reinterpret_cast<const float2 *>(col + i * pu) : make_float2(0.f, 0.f);
+                q[i] = i < NR ? ld_pair<TS>(col + i * pu) : make_float2(0.f, 0.f);
 #pragma unroll
             for (int s = 0; s < NR; ++s) {
                 const float2 v = q[s % LA];
-                if (s + LA < NR) q[s % LA] = *reinterpret_cast<const float2 *>(col + (s + LA) * pu);
+                if (s + LA < NR) q[s % LA] = ld_pair<TS>(col + (s + LA) * pu);
                 if (UC && s >= R && s < R + TH) *reinterpret_cast<float2 *>(Uc + (s - R) * pc + c) = v;
                 update(v, s % P);
                 if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
@@ -298,7 +311,7 @@ __device__ __forceinline__ void pass_v2(const float *__restrict__ U, int pu, flo
                 for (int k = 0; k < P; ++k) {
                     const int s = s0 + k;
                     if (s < RH_rt) {
-                        update(*reinterpret_cast<const float2 *>(col + s * pu), k);
+                        update(ld_pair<TS>(col + s * pu), k);
                         if (s >= R) acol[(s - R) * (pa >> 1)] = acc;
                     }
                 }
@@ -707,19 +720,23 @@ __device__ __forceinline__ void tile_origin(const Fwd2Params &p, int tile, int &
 // zeros beyond it, and tiles touching its border then set every frame cell outside the
 // image to its nearest image cell (the appendix's replicate pad), which always lies in
 // the same box -- no separate padding pass.
-// EARLY (float32 frame to frame, R % 4 == 0, no maps): pass V copies the centre rows that
-// pass H reads, so the next tile's load is issued before pass H instead of after it and
-// lands while pass H runs; results leave by 32-byte register stores (the frame's columns
-// at a segment start lie on 32 bytes: no grid shift, a 32-float row pitch), which frees
-// the tensor-store staging for the copy.
+// EARLY (single passes without maps: float32 frame to frame at R % 4 == 0, 16-bit storage
+// at any R): pass V copies the centre rows that pass H reads (16-bit sources widened in
+// registers, so no float copy of the whole box is made), and the next tile's load is
+// issued before pass H instead of after it and lands while pass H runs.  Float32 results
+// leave by 32-byte register stores (the frame's columns at a segment start lie on 32
+// bytes: no grid shift, a 32-float row pitch), which frees the tensor-store staging for
+// the copy; 16-bit results by the 16-byte register stores of the other 16-bit kernels.
 template <typename T, int R, bool TIE_APP, bool MAPS, bool DIRECT, bool FAST = false, bool TSTORE = false,
           bool XSTAGE = false, bool PADIN = false, bool EARLY = false>
-__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !XSTAGE && !EARLY ? 4 : 3) : 2)
+__global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !XSTAGE &&
+                                                !(EARLY && sizeof(T) == 4) ? 4 : 3)
+                                             : 2)
     osbf_fwd2(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dmap, const Fwd2Params p) {
     static_assert(!TSTORE || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0), "tensor stores: float32, R % 4 == 0");
     static_assert(!PADIN || TSTORE, "the padding first pass: the tensor-store kernel");
-    static_assert(!EARLY || (DIRECT && sizeof(T) == 4 && !MAPS && R % 4 == 0 && !TSTORE && !XSTAGE),
-                  "early loads: float32 frame to frame, R % 4 == 0, no maps");
+    static_assert(!EARLY || (DIRECT && !MAPS && !TSTORE && !XSTAGE && (sizeof(T) != 4 || R % 4 == 0)),
+                  "early loads: single passes without maps (float32: R % 4 == 0)");
     extern __shared__ __align__(128) unsigned char smem2[];
     const int D = DIRECT ? 1 : p.D;  // single-pass kernels: the whole layout is a compile-time constant
     const Layout2 L = make_layout2<T>(R, D, DIRECT, TSTORE, MAPS && DIRECT, XSTAGE, EARLY);
@@ -818,7 +835,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
         }
 
         bool prefetched = false;
-        if (sizeof(T) != 4) {  // widen the 16-bit box into the float buffer, then the box is free
+        if (sizeof(T) != 4 && !EARLY) {  // widen the 16-bit box into the float buffer, then the box is free
             const int w4 = (L.PU - 4) / 4;
             for (int i = threadIdx.x; i < L.RH0 * w4; i += NT) {
                 const int y = i / w4, x = (i % w4) * 4;
@@ -840,7 +857,7 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
             const int RH = L.RH0 - 2 * (j - 1) * R, RW = L.RW0 - 2 * (j - 1) * R;
             float *Uc = reinterpret_cast<float *>(smem2 + L.off_uc);
             if (EARLY) {
-                pass_v2<R, TH + 2 * R, true>(Uin, puin, A, L.P2, RH, RW, Uc, L.PU);
+                pass_v2<R, TH + 2 * R, true, T>(bin, L.BX, A, L.P2, RH, RW, Uc, L.PU);
                 __syncthreads();
                 prefetch(tile);  // the input box is dead: its next load overlaps pass H
                 prefetched = true;
@@ -878,12 +895,13 @@ __global__ void __launch_bounds__(NT, DIRECT ? (R <= 9 && !MAPS && !TSTORE && !X
             if (MAPS && p.maps)
                 mplane =
                     p.maps + (long long)(p.map_iter0 + j - 1) * p.map_iter_stride + (long long)plane * p.map_plane;
-            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, false, EARLY>(
+            pass_h2<R, T, TIE_APP, MAPS, DIRECT, FAST, TSTORE, XSTAGE, false, EARLY && sizeof(T) == 4>(
                 EARLY ? Uc : Uin, EARLY ? L.PU : puin, EARLY ? 0 : R, A, L.P2, Uout, L.PU, gdst, p.dst_pitch, g,
                 mplane, sbase, &dmap, smem2 + L.off_ms, reinterpret_cast<float *>(smem2 + L.off_xs));
-            // EARLY: the next load is already out, and the barrier after the next tile's
-            // load wait orders this pass H's reads before the next pass V's writes
-            if (!EARLY) __syncthreads();
+            // single passes whose next load is already out (EARLY, and 16-bit storage, whose
+            // box is widened and freed before pass V): the barrier after the next tile's load
+            // wait orders this pass H's reads before the next tile's shared-memory writes
+            if (!(DIRECT && (EARLY || sizeof(T) != 4))) __syncthreads();
             if (!prefetched) {  // float32: U^0 lived in the TMA box; it is dead after pass 1
                 prefetch(tile);
                 prefetched = true;
