@@ -292,7 +292,8 @@ def form_batched(dev):
             "batched_mpix_iter_s": units / t_b / 1e6, "plain_calls_mpix_iter_s": units / t_p / 1e6,
             "batched_over_plain": t_p / t_b, "p50_latency_ms": 1e3 * lat[len(lat) // 2],
             "p99_latency_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "tuned_policy": {"job_order": "by decreasing work" if pol and pol[0] == 1 else "as given",
+            "tuned_policy": {"job_order": {1: "by decreasing work", 2: "by radius, then decreasing work"}.get(
+                                 pol[0] if pol else 0, "as given"),
                              "ctas_per_sm": pol[1] if pol else None,
                              "batched_mpix_iter_s": units / t_t / 1e6,
                              "p50_latency_ms": 1e3 * lat_t[len(lat_t) // 2],

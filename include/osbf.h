@@ -254,15 +254,17 @@ typedef struct {
 osbf_status osbf_filter_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream);
 
 /* Tune the batched launch of this job list (synchronous; runs the batch several times): time
- * each layout policy -- the job order within every pass round (as given, or by decreasing
- * H x W x passes) and the resident CTAs per SM (as many as fit, or one fewer) -- each from
+ * each layout policy -- the job order within every pass round (as given; by decreasing
+ * H x W x passes; or grouped by radius, then by decreasing work, the untuned default) and
+ * the resident CTAs per SM (as many as fit, or one fewer) -- each from
  * its own cached graph, and record the fastest for the job signature; later
  * osbf_filter_batched() calls with the same jobs replay that policy's graph.  The policy
  * changes the schedule, never the results. */
 osbf_status osbf_autotune_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *stream);
 
-/* The tuned policy of this job list: *order (0 as given, 1 by decreasing work) and
- * *ctas_per_sm; returns 1 if one is recorded, else 0 (the defaults 0, as many as fit). */
+/* The tuned policy of this job list: *order (0 as given, 1 by decreasing work, 2 grouped by
+ * radius, then by decreasing work) and *ctas_per_sm; returns 1 if one is recorded, else 0
+ * (the defaults: 2, as many as fit). */
 int osbf_batched_policy(osbf_ctx *ctx, const osbf_job *jobs, int njobs, int *order, int *ctas_per_sm);
 
 /* Per-image latency of the last osbf_filter_batched() call: for each job of its

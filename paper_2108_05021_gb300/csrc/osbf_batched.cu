@@ -264,10 +264,12 @@ struct Planned {
 };
 
 // How a batch is laid out and launched: the job order within each pass round (0: as given,
-// 1: by decreasing work, H x W x passes, so the longest chains start first) and the
+// 1: by decreasing work, H x W x passes, so the longest chains start first; 2: grouped by
+// radius, then by decreasing work -- CTAs that run at the same time then run the same
+// radius's unrolled sweep, which keeps one variant's code in the instruction cache) and the
 // resident CTAs per SM.  osbf_autotune_batched() times the candidates on the batch itself.
 struct Policy {
-    int order = 0;
+    int order = 2;  // untuned: grouped by radius
     int ctas_per_sm = 0;  // 0: as many as fit
 };
 
@@ -401,8 +403,9 @@ osbf_status batched_run(osbf_ctx *ctx, const osbf_job *jobs, int njobs, void *st
         }
         std::vector<size_t> korder(hj.size());
         for (size_t k = 0; k < hj.size(); ++k) korder[k] = k;
-        if (pol.order == 1)
+        if (pol.order == 1 || pol.order == 2)
             std::stable_sort(korder.begin(), korder.end(), [&](size_t a, size_t b) {
+                if (pol.order == 2 && hj[a].R != hj[b].R) return hj[a].R < hj[b].R;
                 return (long long)hj[a].H * hj[a].W * hj[a].iters > (long long)hj[b].H * hj[b].W * hj[b].iters;
             });
         std::vector<int4> items;
@@ -540,7 +543,7 @@ osbf_status osbf_autotune_batched(osbf_ctx *ctx, const osbf_job *jobs, int njobs
         if (occ < 1) occ = 1;
     }
     std::vector<Policy> cand;
-    for (int order = 0; order < 2; ++order)
+    for (int order = 0; order < 3; ++order)
         for (int c = occ; c >= 1 && c >= occ - 1; --c) {
             Policy p;
             p.order = order;
@@ -584,7 +587,7 @@ int osbf_batched_policy(osbf_ctx *ctx, const osbf_job *jobs, int njobs, int *ord
     const std::vector<long long> sig = job_signature(ctx, jobs, njobs);
     auto it = bs->tuned.find(sig);
     if (it == bs->tuned.end()) {
-        *order = 0;
+        *order = Policy().order;
         *ctas_per_sm = 0;
         return 0;
     }

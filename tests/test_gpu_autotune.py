@@ -85,7 +85,7 @@ def test_autotune_batched_policy_is_replayed():
     osbf.autotune_batched(ins, rs, its, outs)
     pol = osbf.batched_policy(ins, rs, its, outs)
     print(f"\ntuned batched policy (job order, CTAs per SM): {pol}")
-    assert pol is not None and pol[0] in (0, 1) and pol[1] >= 1
+    assert pol is not None and pol[0] in (0, 1, 2) and pol[1] >= 1
     for o in outs:
         o.zero_()
     osbf.batched(ins, rs, its, outputs=outs)  # the tuned policy's cached graph
