@@ -189,20 +189,55 @@ __device__ void crop(const Job &jb, int tile) {
     }
 }
 
+// L2 prefetch of the rows an item will read (a tile's region of the previous frame, of the
+// clamped input for pass 0, or a crop tile's frame rows), one instruction per 128-byte
+// line, spread over the CTA.  The frames of a whole batch do not stay in L2 between pass
+// rounds, so without it every region load waits on DRAM.
+__device__ __forceinline__ void prefetch_rows(const float *base, long long pitch, int y0, int y1, int x0, int x1) {
+    if (y0 >= y1 || x0 >= x1) return;
+    const int l0 = x0 >> 5, l1 = (x1 - 1) >> 5;  // 32 floats per 128-byte line
+    const int nl = l1 - l0 + 1, n = (y1 - y0) * nl;
+    for (int e = threadIdx.x; e < n; e += v2::NT) {
+        const int y = y0 + e / nl, l = l0 + e % nl;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long long)y * pitch + (long long)l * 32));
+    }
+}
+
+__device__ void prefetch_item(const Job &jb, int g, int tile, int crop_item) {
+    if (crop_item) {
+        const int ty0 = (tile / jb.tiles_x) * v2::TH, tx0 = (tile % jb.tiles_x) * v2::TW - jb.shift;
+        prefetch_rows(jb.frame[(jb.iters - 1) & 1], jb.FWp, max(ty0, jb.R), min(ty0 + v2::TH, jb.R + jb.H),
+                      max(tx0, jb.R), min(tx0 + v2::TW, jb.R + jb.W));
+        return;
+    }
+    const v2::Layout2 L = v2::make_layout2<float>(jb.R, 1, true);
+    const bool og = jb.out_grid && g == jb.iters - 1;
+    const int ty0 = og ? (tile / jb.tiles_x_last) * v2::TH + jb.R : (tile / jb.tiles_x) * v2::TH;
+    const int tx0 = og ? (tile % jb.tiles_x_last) * v2::TW + jb.R : (tile % jb.tiles_x) * v2::TW - jb.shift;
+    const int fy0 = ty0 - L.EY, fx0 = tx0 - L.EX;
+    if (g == 0)  // the region's frame rows and columns, clamped into the unpadded input
+        prefetch_rows(jb.in, jb.W, max(fy0 - jb.R, 0), min(fy0 + L.RH0 - jb.R, jb.H), max(fx0 - jb.R, 0),
+                      min(fx0 + L.BX - jb.R, jb.W));
+    else
+        prefetch_rows(jb.frame[(g - 1) & 1], jb.FWp, max(fy0, 0), min(fy0 + L.RH0, jb.FH), max(fx0, 0),
+                      min(fx0 + L.BX, jb.FW));
+}
+
 __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
     extern __shared__ __align__(128) unsigned char bsmem[];
-    __shared__ int s_item;
+    __shared__ int s_item, s_next;
     __shared__ int s_fail;
     if (threadIdx.x == 0) {
         atomicMin(p.t_start, now_ns());
         s_fail = 0;
+        s_item = atomicAdd(p.next, 1);
     }
-    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(p.next, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= p.nitems) break;
+        // the item after this one is taken now, so its rows can be prefetched during this one
+        if (threadIdx.x == 0) s_next = atomicAdd(p.next, 1);
         const int4 it = p.items[item];
         const Job jb = p.jobs[it.x];
         const int g = it.y;
@@ -223,6 +258,13 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
         }
         __syncthreads();
         if (s_fail) break;
+        {
+            const int nx = s_next;
+            if (nx < p.nitems) {
+                const int4 it2 = p.items[nx];
+                prefetch_item(p.jobs[it2.x], it2.y, it2.z, it2.w);
+            }
+        }
         if (it.w) {
             crop(jb, it.z);
         } else {
@@ -244,6 +286,7 @@ __global__ void __launch_bounds__(v2::NT) osbf_batched_kernel(const Params p) {
             __threadfence();
             const int prev = atomicAdd(p.done + jb.cnt_base + g, 1);
             if (it.w && prev + 1 == jb.ntiles) p.t_done[it.x] = now_ns();
+            s_item = s_next;
         }
     }
 }
