@@ -253,8 +253,14 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     // (the tile grid shifts so the halo stays exactly r columns while the TMA box starts
     // on 16 bytes)
     const bool last_out = gl.dst_is_output != 0;
-    const bool out_ok = !last_out || (W % 4 == 0 && r % 4 == 0 &&
-                                      ((uintptr_t)gl.dst % (st == Storage::F32 ? 16 : 8)) == 0);
+    // the cropped output's rows hold aligned 4-vectors (16-bit kernels and tensor stores need them)
+    const bool out_vec = W % 4 == 0 && r % 4 == 0 && ((uintptr_t)gl.dst % (st == Storage::F32 ? 16 : 8)) == 0;
+    // float32 direct kernels without tensor stores stage their rows and write them one float
+    // per lane, so they take any cropped output; their tile grid (shifted by (4 - r % 4) % 4)
+    // and the fused-pass kernel's (halo rounded up to 4 columns) start every row segment on
+    // the same frame column, so both give the same result bit for bit
+    // (the fast approximation's direct kernel stores 4-vectors from registers: it needs out_vec)
+    const bool out_ok = !last_out || (st == Storage::F32 && !gl.fast) || out_vec;
     const bool direct = Dg == 1 && gl.tie == 0 && out_ok;
     if (gl.fast && (!direct || st != Storage::F32 || gl.variant == 2)) {
         *what = "the fast approximation runs single float32 passes written from registers";
@@ -267,13 +273,13 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     // float32 single passes at r % 4 == 0 of the paper tie order (no maps): results leave by
     // per-warp tensor stores -- into the next frame, or into the cropped output when its
     // rows hold whole 16-byte groups (W % 4 == 0, 16-byte aligned base)
-    const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !gl.maps;
+    const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !gl.maps && (!last_out || out_vec);
     // The pass into the cropped output runs on the tile grid shifted by (r, r): tiles then
     // start at output rows 32k and columns 128k, so every tensor store starts at a
     // non-negative, 16-byte aligned output coordinate.  With maps the same grid, extended
     // by one tile row and column before the output, also covers the frame ring: the plain
     // and the map-writing passes share tile origins (and so their running sums' phases).
-    const bool out_grid = last_out && direct && st == Storage::F32 && r % 4 == 0;
+    const bool out_grid = last_out && direct && st == Storage::F32 && r % 4 == 0 && out_vec;
     const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
     // the streaming strip kernel: float32 single passes of the paper tie order at r <= 8; it
     // writes the cropped output through staged rows (one float per lane), so any W works
