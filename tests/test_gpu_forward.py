@@ -97,7 +97,7 @@ def test_no_maps_kernels_match_oracle(variant, r, W):
     """The kernels a plain call runs (no maps): frame-to-frame passes at r % 4 == 0 leave
     through per-warp tensor stores (r = 4) or the early-load kernel's 32-byte register
     stores (r >= 8); the last pass writes the cropped output with tensor stores on the
-    output-aligned grid when W % 4 == 0 and through the shared-memory kernel otherwise.
+    output-aligned grid when W % 4 == 0 and through staged rows of the direct kernel otherwise.
     Their results equal the map-writing run bit for bit (same arithmetic, so the maps run's
     selections are the no-maps run's), and the oracle, hinted with those maps, agrees
     within 1e-5 on every pixel."""

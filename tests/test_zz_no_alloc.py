@@ -37,7 +37,7 @@ def noalloc(x, r, iters, out=None):
 
 def test_noalloc_matches_filter_on_two_calls():
     # r = 8 with W % 4 == 0: early-load passes and a tensor-store last pass; r = 3 with an odd W:
-    # a shifted tile grid and the last pass through the shared-memory kernel
+    # a shifted tile grid and the last pass through staged rows into the cropped output
     cases = [((1, 3, 200, 300), 8, 4, 11), ((2, 1, 150, 257), 3, 5, 12)]
     for shape, r, iters, seed in cases:
         x_np = synth.piecewise_stack(*shape, seed=seed, sigma=0.05)
