@@ -1,7 +1,8 @@
 // Radius / variant dispatch of the persistent forward kernel (osbf_fwd2.cuh), shared by
 // the per-storage-type translation units (fwd2_f32.cu, fwd2_f16.cu, fwd2_bf16.cu).
 //   direct : one pass per launch written from registers into the destination
-//            (paper tie order; with or without maps)
+//            (paper tie order; float32 also the appendix order, fwd2_app.cu; with or
+//            without maps)
 //   general: fused passes through shared memory (both tie orders; maps for the
 //            appendix order only where APP_MAPS)
 #pragma once
@@ -20,6 +21,10 @@ template <typename T> constexpr bool kEarly = sizeof(T) == 2;
 template <typename T, bool APP_MAPS>
 cudaError_t launch_fwd2_t(int R, bool tie_app, bool maps, bool direct, const CUtensorMap &src,
                           const v2::Fwd2Params &p, int grid, cudaStream_t s) {
+    if (direct && tie_app) {  // float32 only (fwd2_app.cu)
+        if constexpr (sizeof(T) == 4) return launch_fwd2_app_f32(R, maps, src, p, grid, s);
+        return cudaErrorInvalidValue;
+    }
     switch (R) {
 #define OSBF_CASE(RR)                                                                                    \
     case RR:                                                                                             \
@@ -41,6 +46,10 @@ cudaError_t launch_fwd2_t(int R, bool tie_app, bool maps, bool direct, const CUt
 
 template <typename T, bool APP_MAPS>
 int occupancy_fwd2_t(int R, bool tie_app, bool maps, bool direct, int D) {
+    if (direct && tie_app) {
+        if constexpr (sizeof(T) == 4) return occupancy_fwd2_app_f32(R, maps);
+        return 0;
+    }
     switch (R) {
 #define OSBF_CASE(RR)                                                                     \
     case RR:                                                                              \

@@ -261,7 +261,8 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     // the same frame column, so both give the same result bit for bit
     // (the fast approximation's direct kernel stores 4-vectors from registers: it needs out_vec)
     const bool out_ok = !last_out || (st == Storage::F32 && !gl.fast) || out_vec;
-    const bool direct = Dg == 1 && gl.tie == 0 && out_ok;
+    // (the appendix tie order has single-pass kernels in float32 only)
+    const bool direct = Dg == 1 && (gl.tie == 0 || st == Storage::F32) && out_ok;
     if (gl.fast && (!direct || st != Storage::F32 || gl.variant == 2)) {
         *what = "the fast approximation runs single float32 passes written from registers";
         return cudaErrorInvalidValue;
@@ -273,13 +274,13 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     // float32 single passes at r % 4 == 0 of the paper tie order (no maps): results leave by
     // per-warp tensor stores -- into the next frame, or into the cropped output when its
     // rows hold whole 16-byte groups (W % 4 == 0, 16-byte aligned base)
-    const bool tstore = direct && st == Storage::F32 && r % 4 == 0 && !gl.maps && (!last_out || out_vec);
+    const bool tstore = direct && gl.tie == 0 && st == Storage::F32 && r % 4 == 0 && !gl.maps && (!last_out || out_vec);
     // The pass into the cropped output runs on the tile grid shifted by (r, r): tiles then
     // start at output rows 32k and columns 128k, so every tensor store starts at a
     // non-negative, 16-byte aligned output coordinate.  With maps the same grid, extended
     // by one tile row and column before the output, also covers the frame ring: the plain
     // and the map-writing passes share tile origins (and so their running sums' phases).
-    const bool out_grid = last_out && direct && st == Storage::F32 && r % 4 == 0 && out_vec;
+    const bool out_grid = last_out && direct && gl.tie == 0 && st == Storage::F32 && r % 4 == 0 && out_vec;
     const int shift = !direct ? 0 : st == Storage::F32 ? (4 - r % 4) % 4 : (8 - r % 8) % 8;
     // the streaming strip kernel: float32 single passes of the paper tie order at r <= 8; it
     // writes the cropped output through staged rows (one float per lane), so any W works

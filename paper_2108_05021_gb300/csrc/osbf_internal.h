@@ -43,6 +43,11 @@ cudaError_t launch_fwd2_fast(int R, bool maps, const CUtensorMap &src, const v2:
                              cudaStream_t s);
 int occupancy_fwd2_fast(int R, bool maps);
 
+// single-pass float32 launches of the appendix tie order (results and selections staged)
+cudaError_t launch_fwd2_app_f32(int R, bool maps, const CUtensorMap &src, const v2::Fwd2Params &p, int grid,
+                                cudaStream_t s);
+int occupancy_fwd2_app_f32(int R, bool maps);
+
 // single-pass float32 launches with per-warp tensor stores (R % 4 == 0, paper tie order, no maps)
 // padin: the first pass straight from the unpadded image (replicate pad in the kernel)
 cudaError_t launch_fwd2_tstore(int R, bool fast, const CUtensorMap &src, const CUtensorMap &dmap,

@@ -219,6 +219,21 @@ def test_tie_order_appendix():
         check_f32(x, r, 4, tie="paper", max_hinted_frac=0.05)
 
 
+@pytest.mark.parametrize("r", [3, 4, 8, 12])
+@pytest.mark.parametrize("W", [256, 301])
+def test_appendix_order_single_pass(r, W):
+    """The appendix tie order's float32 single-pass kernels (plain and map-writing, results
+    and selections staged; every pass, also the last into the cropped output at any W):
+    several planes, many tiles, plain == map-writing bit for bit, and the oracle in the
+    appendix order, hinted with the run's maps, within 1e-5.  A depth-2 run (the fused-pass
+    kernel) agrees with the oracle as well."""
+    x = synth.piecewise_stack(1, 2, 97, W, seed=90 + r, sigma=0.05)
+    plain, _ = gpu_filter(x, r, 4, tie="appendix", want_maps=False)
+    out, maps, ref = check_f32(x, r, 4, tie="appendix")
+    np.testing.assert_array_equal(plain, out)
+    check_f32(x, r, 4, depth=2, tie="appendix")
+
+
 def test_edges_corners_checkerboard_preserved():
     """Paper-stated invariants, at a size spanning many tiles."""
     for r in (2, 8):
