@@ -248,10 +248,9 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
     const int r = gl.r, Dg = gl.D, P = gl.P, H = gl.H, W = gl.W;
     const int FH = H + 2 * r, FW = W + 2 * r;
     *what = "forward launch failed";
-    // one pass written straight from registers into the destination: a frame, or the
-    // cropped output when its rows hold aligned 4-vectors (W % 4 == 0, r % 4 == 0); any r
-    // (the tile grid shifts so the halo stays exactly r columns while the TMA box starts
-    // on 16 bytes)
+    // Direct: one pass written from registers (or staged rows) into the destination, a
+    // frame or the cropped output; any r (the tile grid shifts so the halo stays exactly r
+    // columns while the TMA box starts on 16 bytes).
     const bool last_out = gl.dst_is_output != 0;
     // the cropped output's rows hold aligned 4-vectors (16-bit kernels and tensor stores need them)
     const bool out_vec = W % 4 == 0 && r % 4 == 0 && ((uintptr_t)gl.dst % (st == Storage::F32 ? 16 : 8)) == 0;
@@ -267,13 +266,10 @@ cudaError_t osbf::launch_group(const GroupLaunch &gl, cudaStream_t s, const char
         *what = "the fast approximation runs single float32 passes written from registers";
         return cudaErrorInvalidValue;
     }
-    // float32 single passes at r % 4 == 0 (no maps) from frame to frame: results leave
-    // through per-warp tensor stores of 32 x 32 segments instead of per-lane 16-byte
-    // stores (the last pass, into the cropped output, stages its rows instead, on the
-    // same tile grid, so every call path shares one summation order)
     // float32 single passes at r % 4 == 0 of the paper tie order (no maps): results leave by
-    // per-warp tensor stores -- into the next frame, or into the cropped output when its
-    // rows hold whole 16-byte groups (W % 4 == 0, 16-byte aligned base)
+    // per-warp tensor stores of 32 x 32 segments -- into the next frame, or into the
+    // cropped output when its rows hold whole 16-byte groups (W % 4 == 0, 16-byte aligned
+    // base); frame-to-frame passes at r >= 8 take the early-load kernel instead (below)
     const bool tstore = direct && gl.tie == 0 && st == Storage::F32 && r % 4 == 0 && !gl.maps && (!last_out || out_vec);
     // The pass into the cropped output runs on the tile grid shifted by (r, r): tiles then
     // start at output rows 32k and columns 128k, so every tensor store starts at a
