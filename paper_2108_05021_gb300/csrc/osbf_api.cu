@@ -414,6 +414,14 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
     }
     if (D > OSBF_MAX_DEPTH) D = OSBF_MAX_DEPTH;
     D = fit_depth(ctx, st, r, D);
+    // 16-bit single passes write the cropped output from registers only where its rows hold
+    // aligned 4-vectors (r % 4 == 0, W % 4 == 0, base on 8 bytes); otherwise their last
+    // pass writes a frame and a crop follows (the fused-pass kernel, the other way to
+    // write the output, takes about three times as long for that pass; both start every
+    // row segment on the same frame column, so the result is the same)
+    const bool half_crop = st != Storage::F32 && !out_is_frame && D == 1 && tie == 0 &&
+                           !(W % 4 == 0 && r % 4 == 0 && ((uintptr_t)out & 7) == 0);
+    const bool crop_last = fast_crop || half_crop;
     if (smem_v2(st, r, 1) > ctx->smem_optin) return fail(ctx, OSBF_EUNSUPPORTED, "tile does not fit shared memory");
 
     // frame buffers: the padded input and the ping-pong targets
@@ -523,7 +531,7 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
         gl.src_is_image = pad_fused && passes == 0;
         gl.fast = fast ? 1 : 0;
         int nxt = -1;
-        if (last && !out_is_frame && !fast_crop) {
+        if (last && !out_is_frame && !crop_last) {
             gl.dst = out;
             gl.dst_is_output = 1;
         } else if (last && out_is_frame) {
@@ -547,8 +555,9 @@ osbf_status osbf_forward_run(osbf_ctx *ctx, const void *in, int in_is_frame, int
             src_pitch = FWp;
         }
     }
-    if (fast_crop) {
-        cudaError_t e = launch_crop_f32((const float *)fb[cur], (float *)out, P, H, W, r, FWp, s);
+    if (crop_last) {
+        cudaError_t e = st == Storage::F32 ? launch_crop_f32((const float *)fb[cur], (float *)out, P, H, W, r, FWp, s)
+                                           : launch_crop_16(fb[cur], out, P, H, W, r, FWp, s);
         if (e != cudaSuccess) return fail(ctx, OSBF_ECUDA, "crop launch failed: %s", cudaGetErrorString(e));
         ctx->last_launches += 1;
     }

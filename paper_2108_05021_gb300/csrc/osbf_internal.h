@@ -109,6 +109,8 @@ int strip_box_width(int R);
 
 // the final crop of a float32 frame into H x W planes (osbf_misc.cu)
 cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W, int R, int FWp, cudaStream_t s);
+// the same for 16-bit storage (FWp in elements)
+cudaError_t launch_crop_16(const void *frame, void *out, int P, int H, int W, int R, int FWp, cudaStream_t s);
 
 // elementwise helpers (osbf_misc.cu)
 cudaError_t launch_u8_to_f32(const uint8_t *in, float *out, long long n, cudaStream_t s);

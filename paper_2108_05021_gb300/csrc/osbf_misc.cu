@@ -120,25 +120,36 @@ cudaError_t launch_pad_replicate(Storage st, const void *in, void *frame, int P,
 
 namespace osbf {
 
-// The appendix's final crop: frame rows/columns r .. r+H-1 / r .. r+W-1 into the output.
-__global__ void crop_f32_kernel(const float *__restrict__ frame, float *__restrict__ out, int H, int W, int R,
-                                int FH, int FWp) {
+// The appendix's final crop: frame rows/columns r .. r+H-1 / r .. r+W-1 into the output
+// (E: the storage element; 16-bit values are copied as they are).
+template <typename E>
+__global__ void crop_kernel(const E *__restrict__ frame, E *__restrict__ out, int H, int W, int R, int FH, int FWp) {
     const int y = blockIdx.y, plane = blockIdx.z;
-    const float *src = frame + ((long long)plane * FH + y + R) * FWp + R;
-    float *dst = out + ((long long)plane * H + y) * W;
+    const E *src = frame + ((long long)plane * FH + y + R) * FWp + R;
+    E *dst = out + ((long long)plane * H + y) * W;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) dst[x] = src[x];
 }
 
-cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W, int R, int FWp, cudaStream_t s) {
+template <typename E>
+static cudaError_t launch_crop(const E *frame, E *out, int P, int H, int W, int R, int FWp, cudaStream_t s) {
     for (int p0 = 0; p0 < P; p0 += 65535) {
         const int np = P - p0 < 65535 ? P - p0 : 65535;
         dim3 grid((W + 255) / 256 < 8 ? (W + 255) / 256 : 8, H, np);
-        crop_f32_kernel<<<grid, 256, 0, s>>>(frame + (size_t)p0 * (H + 2 * R) * FWp, out + (size_t)p0 * H * W, H, W,
-                                              R, H + 2 * R, FWp);
+        crop_kernel<E><<<grid, 256, 0, s>>>(frame + (size_t)p0 * (H + 2 * R) * FWp, out + (size_t)p0 * H * W, H, W, R,
+                                            H + 2 * R, FWp);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_crop_f32(const float *frame, float *out, int P, int H, int W, int R, int FWp, cudaStream_t s) {
+    return launch_crop<float>(frame, out, P, H, W, R, FWp, s);
+}
+
+cudaError_t launch_crop_16(const void *frame, void *out, int P, int H, int W, int R, int FWp, cudaStream_t s) {
+    return launch_crop<uint16_t>(static_cast<const uint16_t *>(frame), static_cast<uint16_t *>(out), P, H, W, R, FWp,
+                                 s);
 }
 
 }  // namespace osbf
